@@ -1,0 +1,219 @@
+"""ctypes front end of the CPU FP64 oracle (``ia_oracle.c``).
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this module. It shares no
+code with the CUDA library; both receive the same seeded initial conditions from
+``paper_2509_15117_gb300.inputs``.
+
+The C source restates the method of arXiv 2509.15117: Eq. 1's equations of motion, V(r) = C8/r^8 -
+C4/r^4 with C4 = alpha/2 and C8 = C4^2/(4 D_e), the Dormand-Prince 5(4) integrator of Dormand & Prince
+(1980) / Shampine & Reichelt (1997) with ode45's step control, the outward crossing of r0 as the end
+of a head-on or thermal trajectory, and the Fig. 1 observables.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ia_oracle.c")
+_LIB = os.path.join(_HERE, "libia_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=c11"]
+
+# status bits of the oracle (its own numbering; the CUDA library defines its own)
+EXIT = 0
+TMAX = 1 << 0
+MAX_STEPS = 1 << 1
+H_UNDERFLOW = 1 << 2
+NONFINITE = 1 << 3
+BAD_IC = 1 << 4
+EXIT_OUTSIDE = 1 << 5
+COMPLEX = 1 << 8
+
+
+class OrcSystem(ctypes.Structure):
+    _fields_ = [
+        ("m_ion", ctypes.c_double), ("m_atom", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("De", ctypes.c_double),
+        ("Omega", ctypes.c_double),
+        ("a", ctypes.c_double * 3), ("q", ctypes.c_double * 3),
+        ("r0", ctypes.c_double), ("t_max", ctypes.c_double),
+        ("rtol", ctypes.c_double), ("atol_pos", ctypes.c_double), ("atol_vel", ctypes.c_double),
+        ("h_max", ctypes.c_double),
+        ("rf_sign", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("max_attempts", ctypes.c_int64),
+    ]
+
+
+class OrcResult(ctypes.Structure):
+    _fields_ = [
+        ("theta_s", ctypes.c_double), ("dp", ctypes.c_double), ("dE_ion", ctypes.c_double),
+        ("t_final", ctypes.c_double), ("t_first_bounce", ctypes.c_double),
+        ("t_last_bounce", ctypes.c_double), ("y_final", ctypes.c_double * 12),
+        ("n_steps", ctypes.c_int64), ("n_rej", ctypes.c_int64),
+        ("n_bounce", ctypes.c_int32), ("status", ctypes.c_uint32),
+    ]
+
+
+RESULT_DTYPE = np.dtype([
+    ("theta_s", "<f8"), ("dp", "<f8"), ("dE_ion", "<f8"), ("t_final", "<f8"),
+    ("t_first_bounce", "<f8"), ("t_last_bounce", "<f8"), ("y_final", "<f8", (12,)),
+    ("n_steps", "<i8"), ("n_rej", "<i8"), ("n_bounce", "<i4"), ("status", "<u4"),
+])
+assert RESULT_DTYPE.itemsize == ctypes.sizeof(OrcResult)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into ``oracle/libia_oracle.so`` (in-tree, git-ignored)."""
+    with _lock:
+        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+            return _LIB
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER
+        d = ctypes.c_double
+        dp = P(ctypes.c_double)
+        L.orc_run_batch.argtypes = [P(OrcSystem), ctypes.c_int32, P(ctypes.c_int32), dp, dp,
+                                    ctypes.c_int64, P(OrcResult), ctypes.c_int32]
+        L.orc_run_batch.restype = None
+        L.orc_potential.argtypes = [P(OrcSystem), d, dp, dp]
+        L.orc_ionatom_rhs.argtypes = [P(OrcSystem), d, d, dp, dp]
+        L.orc_ion_energy.argtypes = [P(OrcSystem), d, d, dp]
+        L.orc_ion_energy.restype = d
+        L.orc_test_solve.argtypes = [ctypes.c_int32, d, d, d, d, d, dp, P(ctypes.c_int64), P(ctypes.c_int64)]
+        L.orc_test_fixed.argtypes = [ctypes.c_int32, d, d, ctypes.c_int64, dp, dp]
+        L.orc_test_dense.argtypes = [ctypes.c_int32, d, d, d, dp, dp]
+        L.orc_ionatom_fixed.argtypes = [P(OrcSystem), d, d, d, ctypes.c_int64, dp]
+        L.orc_ionatom_segment.argtypes = [P(OrcSystem), d, d, d, dp, P(ctypes.c_int64), P(ctypes.c_int64)]
+        L.orc_max_threads.restype = ctypes.c_int32
+        _lib = L
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_system(desc: dict) -> OrcSystem:
+    """Oracle system struct from a descriptor dict (keys of ``inputs.SystemDesc``)."""
+    s = OrcSystem()
+    s.m_ion = desc["m_ion"]
+    s.m_atom = desc["m_atom"]
+    s.alpha = desc["alpha"]
+    s.De = desc["De"]
+    s.Omega = desc["Omega"]
+    for j in range(3):
+        s.a[j] = desc["a"][j]
+        s.q[j] = desc["q"][j]
+    s.r0 = desc["r0"]
+    s.t_max = desc["t_max"]
+    s.rtol = desc["rtol"]
+    s.atol_pos = desc["atol_pos"]
+    s.atol_vel = desc["atol_vel"]
+    s.h_max = desc["h_max"]
+    s.rf_sign = int(desc.get("rf_sign", 1))
+    s.max_attempts = int(desc.get("max_attempts", 50_000_000))
+    return s
+
+
+def max_threads() -> int:
+    return int(lib().orc_max_threads())
+
+
+def run_batch(systems, y0, phi0, sys_id=None, nthreads: int = 0) -> np.ndarray:
+    """Integrate every trajectory; returns a structured array with ``RESULT_DTYPE``.
+
+    systems: list of descriptor dicts; y0: (n, 12) float64; phi0: (n,) float64; sys_id: (n,) int32.
+    """
+    L = lib()
+    y0 = np.ascontiguousarray(y0, dtype=np.float64)
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+    n = y0.shape[0]
+    assert y0.shape == (n, 12) and phi0.shape == (n,)
+    arr = (OrcSystem * len(systems))(*[make_system(d) for d in systems])
+    sid_ptr = None
+    if sys_id is not None:
+        sys_id = np.ascontiguousarray(sys_id, dtype=np.int32)
+        assert sys_id.shape == (n,)
+        sid_ptr = sys_id.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    out = np.zeros(n, dtype=RESULT_DTYPE)
+    L.orc_run_batch(arr, len(systems), sid_ptr, _dptr(y0), _dptr(phi0), n,
+                    out.ctypes.data_as(ctypes.POINTER(OrcResult)), int(nthreads))
+    return out
+
+
+def potential(desc: dict, r: float):
+    s = make_system(desc)
+    V = ctypes.c_double()
+    dV = ctypes.c_double()
+    lib().orc_potential(ctypes.byref(s), r, ctypes.byref(V), ctypes.byref(dV))
+    return V.value, dV.value
+
+
+def rhs(desc: dict, phi0: float, t: float, y) -> np.ndarray:
+    s = make_system(desc)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    f = np.zeros(12)
+    lib().orc_ionatom_rhs(ctypes.byref(s), phi0, t, _dptr(y), _dptr(f))
+    return f
+
+
+def ion_energy(desc: dict, phi0: float, t: float, y) -> float:
+    s = make_system(desc)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    return float(lib().orc_ion_energy(ctypes.byref(s), phi0, t, _dptr(y)))
+
+
+def test_solve(kind: int, p: float, t_end: float, y0, rtol: float, atol: float, hmax: float):
+    y = np.array(y0, dtype=np.float64)
+    ns = ctypes.c_int64()
+    nr = ctypes.c_int64()
+    lib().orc_test_solve(kind, p, t_end, rtol, atol, hmax, _dptr(y), ctypes.byref(ns), ctypes.byref(nr))
+    return y, ns.value, nr.value
+
+
+def test_fixed(kind: int, p: float, h: float, nsteps: int, y0):
+    y = np.array(y0, dtype=np.float64)
+    err = np.zeros_like(y)
+    lib().orc_test_fixed(kind, p, h, nsteps, _dptr(y), _dptr(err))
+    return y, err
+
+
+def test_dense(kind: int, p: float, h: float, s: float, y0):
+    y = np.array(y0, dtype=np.float64)
+    out = np.zeros_like(y)
+    lib().orc_test_dense(kind, p, h, s, _dptr(y), _dptr(out))
+    return out
+
+
+def ionatom_fixed(desc: dict, phi0: float, t0: float, h: float, nsteps: int, y0) -> np.ndarray:
+    s = make_system(desc)
+    y = np.array(y0, dtype=np.float64)
+    lib().orc_ionatom_fixed(ctypes.byref(s), phi0, t0, h, nsteps, _dptr(y))
+    return y
+
+
+def ionatom_segment(desc: dict, phi0: float, t0: float, t1: float, y0):
+    s = make_system(desc)
+    y = np.array(y0, dtype=np.float64)
+    ns = ctypes.c_int64()
+    nr = ctypes.c_int64()
+    lib().orc_ionatom_segment(ctypes.byref(s), phi0, t0, t1, _dptr(y), ctypes.byref(ns), ctypes.byref(nr))
+    return y, ns.value, nr.value
