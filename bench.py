@@ -1,0 +1,366 @@
+"""Benchmark: trajectories/s and RHS evaluations/s of the ion-atom trajectory engine (FP64, rtol 1e-10).
+
+Workload: the head-on species x energy sweep (Yb+ with Li, Na, K, Rb, Cs; 8 energies log-spaced from
+1 uK to 1 mK; D_e = 1 K, q = 0.1, a = 0, t_max = 1 ms) on the cell-centred 1024 x 1024 (theta, phi)
+octant grid. One step integrates one batch: every `stride`-th grid point in each direction of all
+40 (species, energy) systems, with the grid offset advanced every step so successive steps see
+different trajectories. Trajectory lengths differ by 10-100x, so the persistent kernel with work-queue
+refill is the timed path; the plain one-thread-per-trajectory kernel is timed on the same batch for
+the speedup.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--stride S]
+Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2509_15117_gb300 import inputs as I  # noqa: E402
+
+METRIC = "trajectories/s and RHS evals/s at rtol 1e-10 FP64, plain vs batched/adjoint"
+UNIT = "trajectories/s"
+GRID = 1024
+
+# FP64 floating-point operations per attempted DP5 step of the kernel (fused multiply-add = 2),
+# counted by ncu's per-thread FP64 instruction counters (2 dfma + dmul + dadd, predicated-on threads)
+# on the persistent kernel, divided by the attempted steps of that launch. See profiles/.
+FLOPS_PER_ATTEMPT = 895.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--stride", type=int, default=4, help="grid stride of the per-step batch")
+    p.add_argument("--warmup-stride", type=int, default=16)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--block", type=int, default=0)
+    p.add_argument("--refill", type=int, default=0)
+    p.add_argument("--blocks-per-sm", type=int, default=0)
+    p.add_argument("--regs-variant", type=int, default=0)
+    p.add_argument("--slice-budget", type=int, default=0)
+    p.add_argument("--tail-group", type=int, default=0)
+    p.add_argument("--tail-blocks-per-sm", type=int, default=0)
+    p.add_argument("--profile-case", action="store_true",
+                   help="run the persistent and plain kernels once on a small batch (for ncu) and exit")
+    return p.parse_args()
+
+
+def profile_case():
+    """Small fixed case for ncu captures: 4096 head-on Rb trajectories at 1 mK on a 64 x 64 octant grid
+    (short, single-bounce dominated), run once by the persistent kernel and once by the plain kernel."""
+    import torch
+    from paper_2509_15117_gb300 import binding as Bd
+    systems = I.c2_systems()
+    rb_hot = [s for (sp, E, s) in systems if sp == "Rb"][-1]
+    th, ph = I.octant_grid(64)
+    v0 = I.speed_for_energy(I.kelvin(I.C2_ENERGIES_K[-1]), rb_hot.m_atom)
+    y0 = I.head_on(th, ph, rb_hot.r0, v0)
+    with Bd.System([rb_hot.as_dict()]) as S:
+        for kernel in (Bd.IA_KERNEL_PERSISTENT, Bd.IA_KERNEL_PLAIN):
+            out = S.run(y0, np.zeros(len(y0)), None, kernel=kernel)
+    torch.cuda.synchronize()
+    n = int(out["n_steps"].sum().item() + out["n_rej"].sum().item())
+    print(json.dumps({"profile_case": "Rb 1 mK head-on 64x64", "trajectories": len(y0), "attempted_steps": n}))
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def batch(step: int, stride: int, rank: int = 0, world: int = 1):
+    """Batch of a step: one grid offset per (step, rank) pair; disjoint across ranks."""
+    k = step * world + rank
+    off = k % stride
+    systems, y0, phi0, sid = I.c2_workload(n_grid=GRID, stride=stride, offset=off)
+    return systems, y0, phi0, sid
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, max clock, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(seconds: float):
+    """The oracle, as it stands, on all host cores, over a bounded sample of the same workload:
+    trajectories drawn evenly from the first step's batch until about `seconds` of CPU work."""
+    from oracle import oracle as O
+    systems, y0, phi0, sid = batch(0, 4)
+    descs = [s.as_dict() for s in systems]
+    n_all = len(y0)
+    cores = O.max_threads()
+    rng = np.random.default_rng(12345)
+    order = rng.permutation(n_all)
+    done = 0
+    t_used = 0.0
+    steps = 0
+    chunk = max(cores * 4, 64)
+    while t_used < seconds and done < n_all:
+        idx = np.sort(order[done:done + chunk])
+        t0 = time.perf_counter()
+        r = O.run_batch(descs, y0[idx], phi0[idx], sid[idx], nthreads=cores)
+        t_used += time.perf_counter() - t0
+        steps += int(np.sum(r["n_steps"] + r["n_rej"]))
+        done += len(idx)
+        chunk = min(chunk * 2, 4096)
+    rate = done / t_used
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "rhs_evals_per_s": (6 * steps + done) / t_used,
+            "sample": f"{done} trajectories drawn uniformly at random (seed 12345) from the step-0 batch "
+                      f"(species x energy sweep, grid stride 4), {t_used:.1f} s on {cores} threads"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cb = cpu_baseline(max(args.cpu_seconds, 5.0) / max(args.steps, 1) * max(args.steps, 1))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "Yb+ head-on species x energy sweep (5 species x 8 energies, 1024^2 "
+                               "octant grid, D_e = 1 K, q = 0.1, t_max = 1 ms), bounded sample",
+                   "rtol": 1e-10},
+        "cpu_baseline": cb,
+        "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "rhs_evals_per_s": cb["rhs_evals_per_s"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.profile_case:
+        profile_case()
+        return
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_2509_15117_gb300 import binding as Bd
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    kw = {"block": args.block, "refill": args.refill, "blocks_per_sm": args.blocks_per_sm,
+          "regs_variant": args.regs_variant, "slice_budget": args.slice_budget, "tail_group": args.tail_group,
+          "tail_blocks_per_sm": args.tail_blocks_per_sm}
+
+    # resident inputs for every step (host-side generation outside the timed region)
+    batches = []
+    for s in range(args.steps):
+        systems, y0, phi0, sid = batch(s, args.stride, rank, world)
+        y, p, d = Bd.to_device_soa(y0, phi0, sid)
+        batches.append((systems, y, p, d, len(phi0)))
+    descs = [s.as_dict() for s in batches[0][0]]
+    sysh = Bd.System(descs)
+    Bd.ia_reserve(sysh.handle, max(b[4] for b in batches), kernel=Bd.IA_KERNEL_PERSISTENT,
+                  **{k: v for k, v in kw.items() if k in ("slice_budget",)})
+    n_max = max(b[4] for b in batches)
+    outs = [Bd.alloc_obs(b[4]) for b in batches]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+
+    # warm-up on smaller batches of the same workload
+    for w in range(args.warmup):
+        systems, y0, phi0, sid = batch(1000 + w, args.warmup_stride, rank, world)
+        y, p, d = Bd.to_device_soa(y0, phi0, sid)
+        o = Bd.alloc_obs(len(phi0))
+        Bd.ia_launch(sysh.handle, y, p, d, o, kernel=Bd.IA_KERNEL_PERSISTENT, **kw)
+    torch.cuda.synchronize()
+
+    peak_flops = Bd.ia_fp64_peak(4, 20000)
+
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    clocks.start()
+    t0 = time.perf_counter()
+    for s, (systems, y, p, d, n) in enumerate(batches):
+        flush.zero_()
+        ev[s][0].record(stream)
+        Bd.ia_launch(sysh.handle, y, p, d, outs[s], kernel=Bd.IA_KERNEL_PERSISTENT, **kw)
+        ev[s][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(kern_ms))
+    n_local = sum(b[4] for b in batches)
+    attempts = sum(int((o["n_steps"].to(torch.int64) + o["n_rej"].to(torch.int64)).sum().item()) for o in outs)
+    rhs = 6 * attempts + n_local
+    tmax_ms = total_ms
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax_ms = float(t.item())
+        c = torch.tensor([float(n_local), float(rhs), float(attempts)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(c)
+        n_all, rhs_all, att_all = (float(x) for x in c.tolist())
+    else:
+        n_all, rhs_all, att_all = float(n_local), float(rhs), float(attempts)
+    value = n_all / (tmax_ms / 1e3)
+    achieved = FLOPS_PER_ATTEMPT * attempts / (total_ms / 1e3)
+
+    # plain kernel on the first batch (speedup of the persistent path)
+    plain = None
+    if not args.no_plain:
+        systems, y, p, d, n = batches[0]
+        o = Bd.alloc_obs(n)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        Bd.ia_launch(sysh.handle, y, p, d, o, kernel=Bd.IA_KERNEL_PLAIN)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1)
+        plain = {"value": n / (pms / 1e3), "unit": UNIT, "ms": pms,
+                 "persistent_speedup": (n / (kern_ms[0] / 1e3)) / (n / (pms / 1e3))}
+
+    # end to end through the public API: pinned host inputs -> device -> launch -> host outputs
+    e2e = None
+    if not args.no_e2e:
+        systems, y0, phi0, sid = batch(0, args.stride, rank, world)
+        n = len(phi0)
+        h_y = torch.from_numpy(np.ascontiguousarray(y0.T)).pin_memory()
+        h_p = torch.from_numpy(phi0).pin_memory()
+        h_s = torch.from_numpy(sid).pin_memory()
+        o = Bd.alloc_obs(n)
+        host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in o.items()}
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        y = h_y.to("cuda", non_blocking=True)
+        p = h_p.to("cuda", non_blocking=True)
+        d = h_s.to("cuda", non_blocking=True)
+        Bd.ia_launch(sysh.handle, y, p, d, o, kernel=Bd.IA_KERNEL_PERSISTENT, **kw)
+        for k in o:
+            host_out[k].copy_(o[k], non_blocking=True)
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        h2d = h_y.numel() * 8 + h_p.numel() * 8 + h_s.numel() * 4
+        d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+        e2e = {"value": n * world / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    sysh.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {
+                "workload": f"Yb+ head-on species x energy sweep: Li, Na, K, Rb, Cs x 8 energies 1 uK..1 mK, "
+                            f"D_e = 1 K, q = 0.1, a = 0, Omega = 2 pi 2 MHz, t_max = 1 ms, rtol 1e-10; "
+                            f"1024^2 octant grid, every {args.stride}th point per direction per step",
+                "trajectories_per_step": int(n_all / args.steps), "rtol": 1e-10, "kernel": "persistent",
+                "l2": "256 MiB buffer written before each step (inputs < L2)",
+                "block": args.block or 128, "refill": args.refill or 1,
+                "slice_budget": args.slice_budget or 65536, "tail_group": args.tail_group or 6,
+            },
+            "rhs_evals_per_s": rhs_all / (tmax_ms / 1e3),
+            "attempted_steps_per_trajectory": att_all / n_all,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_flops / 1e12,
+                         "unit": "TFLOP/s", "frac": achieved / peak_flops, "traffic": None,
+                         "peak_source": "FP64 FMA microbenchmark (ia_fp64_peak) measured in this run",
+                         "flops_per_attempted_step": FLOPS_PER_ATTEMPT},
+            "plain": plain,
+            "e2e": e2e,
+            "gpu_launches": args.steps * (1 if args.slice_budget < 0 else 2),
+            "clocks": clk,
+            "wall_s": wall,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * ionatom.h -- C ABI of the GB300 (sm_103a) engine for classical ion-atom trajectories.
+ *
+ * Method: arXiv 2509.15117, "Chaotic scattering and heating in cold ion-atom collisions".
+ *   - Eq. 1 (Hamiltonian): one ion in a Paul trap with the per-axis term
+ *     (a_j + 2 q_j cos(Omega t)) m_i Omega^2 / 8 x_j^2, one atom, interaction V(|x_a - x_i|);
+ *     read with x_j the ion's Cartesian coordinate, and generalised to s cos(Omega t + phi0) with an
+ *     rf phase phi0 per trajectory and a sign s (rf_sign, +1 = Eq. 1 as printed).
+ *   - Text after Eq. 1: V(r) = C8/r^8 - C4/r^4, C4 = alpha/2; C8 is fixed by the well depth D_e,
+ *     C8 = C4^2/(4 D_e). The equations for the twelve variables are integrated with the adaptive
+ *     Dormand-Prince 5(4) pair (Dormand & Prince 1980; Shampine & Reichelt 1997, i.e. ode45).
+ *   - Head-on paragraph: trajectories start on the sphere of radius r0 and end when the ion-atom
+ *     separation crosses r0 outward (or at t_max).
+ *   - Fig. 1 caption: observables -- scattering angle between the atom's initial and final velocity,
+ *     number of bounces (short-range collisions), momentum transfer |p_f - p_i| of the atom; the
+ *     text adds the ion energy change (heating) and complex formation (more than one bounce).
+ *
+ * Conventions for every entry point:
+ *   - Units are atomic units (a0, E_h, m_e, a.u. of time).
+ *   - State layout: y = [x_ion(3), v_ion(3), x_atom(3), v_atom(3)].
+ *   - Device arrays are structure-of-arrays: component c of trajectory i sits at p[c * ld + i].
+ *     Every device pointer must be 8-byte aligned; ld >= n.
+ *   - The caller owns every device buffer it passes and the CUDA stream; calls are asynchronous on
+ *     that stream (results are valid after the caller synchronises it). The library owns only what
+ *     ia_system_create allocates (the parameter table and a work counter), freed by
+ *     ia_system_destroy.
+ *   - Functions return IA_OK (0) or a negative IA_ERR_* code; no exception crosses the ABI.
+ *     ia_error_string() names a code. A CUDA launch failure is reported as IA_ERR_CUDA.
+ *   - Per-trajectory failures are not errors of the call: they are status bits in the output.
+ */
+#ifndef IONATOM_H
+#define IONATOM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define IA_OK 0
+#define IA_ERR_INVALID_ARG (-1)   /* NULL pointer, n < 0, ld < n, bad option value */
+#define IA_ERR_BAD_DESC (-2)      /* a system descriptor fails validation */
+#define IA_ERR_CUDA (-3)          /* a CUDA runtime call failed */
+#define IA_ERR_ALIGNMENT (-4)     /* a device pointer is not 8-byte aligned */
+#define IA_ERR_NO_DEVICE (-5)     /* no CUDA device, or not an sm_103 device */
+#define IA_ERR_TOO_LARGE (-6)     /* size beyond a documented limit */
+
+/* ---- per-trajectory status bits (ia_obs_soa.status) ---- */
+#define IA_ST_EXIT 0u                 /* separation crossed r0 outward; observables at the crossing */
+#define IA_ST_TMAX (1u << 0)          /* reached t_max; observables at t_max */
+#define IA_ST_MAX_STEPS (1u << 1)     /* attempted-step cap reached */
+#define IA_ST_H_UNDERFLOW (1u << 2)   /* step fell to 16 eps(t) and was still rejected */
+#define IA_ST_NONFINITE (1u << 3)     /* a stage produced inf/nan; observables at the last good state */
+#define IA_ST_BAD_IC (1u << 4)        /* non-finite initial state, zero separation, bad sys_id */
+#define IA_ST_EXIT_OUTSIDE (1u << 5)  /* moving outward beyond r0 with no crossing inside the step */
+#define IA_ST_COMPLEX (1u << 8)       /* n_bounce >= 2 (complex formed) */
+
+/* ---- kernels ---- */
+#define IA_KERNEL_PLAIN 0       /* one thread per trajectory, one launch per batch */
+#define IA_KERNEL_PERSISTENT 1  /* resident grid; finished lanes refill from an atomic work queue */
+
+/* One physical system with its integration settings. */
+typedef struct ia_system_desc {
+    double m_ion, m_atom;   /* masses, m_e (> 0) */
+    double alpha;           /* static dipole polarisability of the atom, a.u. (>= 0); C4 = alpha/2 */
+    double De;              /* well depth, E_h (> 0 if alpha > 0); C8 = C4^2 / (4 De) */
+    double Omega;           /* rf angular frequency, rad per a.u. of time (> 0) */
+    double a[3], q[3];      /* Mathieu parameters per axis */
+    double r0;              /* start sphere and exit radius, a0 (> 0) */
+    double t_max;           /* a.u. of time (> 0) */
+    double rtol;            /* relative tolerance (> 0) */
+    double atol_pos;        /* absolute tolerance of positions, a0 (> 0) */
+    double atol_vel;        /* absolute tolerance of velocities, a.u. (> 0) */
+    double h_max;           /* largest step, a.u. of time (> 0) */
+    int32_t rf_sign;        /* +1 (Eq. 1 as printed) or -1 */
+    int32_t reserved;       /* must be 0 */
+    int64_t max_attempts;   /* cap on attempted steps per trajectory (> 0) */
+} ia_system_desc;
+
+typedef struct ia_system ia_system; /* opaque */
+
+/* Initial conditions (device pointers). */
+typedef struct ia_ic_soa {
+    const double* y0;       /* 12 x ld: initial state at t = 0 */
+    const double* phi0;     /* n: rf phase at t = 0 */
+    const int32_t* sys_id;  /* n: row of the system table, or NULL for row 0 */
+    int64_t ld;             /* leading dimension of y0 (>= n) */
+} ia_ic_soa;
+
+/* Observables (device pointers, written for every trajectory). */
+typedef struct ia_obs_soa {
+    double* theta_s;        /* angle between initial and final atom velocity, rad */
+    double* dp;             /* |p_f - p_i| of the atom, a.u. */
+    double* dE_ion;         /* E_ion(t_f) - E_ion(0), E_ion = kinetic + trap term of Eq. 1, E_h */
+    double* t_final;        /* time of the crossing (or of the stop), a.u. */
+    double* t_first_bounce; /* end time of the step containing the first pericentre (0 if none) */
+    double* t_last_bounce;  /* same for the last pericentre */
+    int32_t* n_bounce;      /* pericentre passages: d.(v_a - v_i) from < 0 to >= 0 */
+    uint32_t* status;       /* IA_ST_* bits */
+    int32_t* n_steps;       /* accepted steps */
+    int32_t* n_rej;         /* rejected steps */
+    double* y_final;        /* 12 x ld final state, or NULL */
+    int64_t ld;             /* leading dimension of y_final (>= n) */
+} ia_obs_soa;
+
+/* Launch options; zero-initialised means defaults. */
+typedef struct ia_launch_opts {
+    int32_t kernel;             /* IA_KERNEL_PLAIN (default) or IA_KERNEL_PERSISTENT */
+    int32_t block;              /* persistent: threads per block, 64, 128 or 256; 0 = 128 (plain: 128) */
+    int32_t grid;               /* persistent: blocks; 0 = resident blocks per SM x SMs */
+    int32_t refill;             /* persistent: idle lanes in a warp before it claims work, 1..32; 0 = 1 */
+    int32_t blocks_per_sm;      /* persistent: resident blocks per SM to use when grid = 0; 0 = max */
+    int32_t regs_variant;       /* persistent: 1 = no register cap (default, 0 means 1); 3 = build capped
+                                   for 3 resident 128-thread blocks per SM (block must be 128) */
+    int32_t slice_budget;       /* persistent: attempted steps after which a trajectory is handed to the
+                                   group-mode tail kernel; 0 = 65536; -1 = never (no tail kernel) */
+    int32_t tail_group;         /* lanes per trajectory in the tail kernel: 6 or 8; 0 = 6 */
+    int32_t tail_blocks_per_sm; /* tail kernel blocks (128 threads) per SM, 1..16; 0 = 1 */
+    int32_t reserved;           /* must be 0 */
+    int64_t suspend_capacity;   /* suspend records; 0 = min(n, max(4096, n/32)). A trajectory that finds
+                                   no free record is finished by its lane. */
+    void* scratch;              /* persistent: caller's device scratch (256-byte aligned), or NULL to use
+                                   the system's own, grown by ia_launch when needed */
+    int64_t scratch_bytes;      /* size of `scratch`; at least ia_scratch_bytes(n, opts) */
+} ia_launch_opts;
+
+/*
+ * Create a table of n_sys systems on the current CUDA device (copied to device memory).
+ * Validation per row: masses, Omega, r0, t_max, tolerances, h_max > 0; alpha >= 0; De > 0 when
+ * alpha > 0; rf_sign = +-1; max_attempts > 0; reserved = 0. Returns IA_ERR_BAD_DESC on failure and
+ * writes nothing to *out. n_sys must be 1..65536.
+ * Derived constants (text after Eq. 1): C4 = alpha/2, C8 = C4^2/(4 De).
+ */
+int ia_system_create(const ia_system_desc* desc, int32_t n_sys, ia_system** out);
+
+/* Free a system table. NULL is accepted. The caller must make sure no launch using it is in flight. */
+int ia_system_destroy(ia_system* sys);
+
+/* Number of rows of a system table, or a negative code. */
+int ia_system_count(const ia_system* sys);
+
+/*
+ * Scratch bytes a persistent launch of n trajectories with these options needs (counters and the
+ * suspend records of trajectories moved to the tail kernel), or a negative code.
+ */
+int64_t ia_scratch_bytes(int64_t n, const ia_launch_opts* opts);
+
+/*
+ * Grow the system's own scratch to what a launch of n trajectories with opts needs (cudaMalloc;
+ * synchronous). Call it before capturing ia_launch into a CUDA graph when opts->scratch is NULL.
+ */
+int ia_reserve(ia_system* sys, int64_t n, const ia_launch_opts* opts);
+
+/*
+ * Integrate n trajectories and write their observables (Eq. 1 with V, DP5(4), exit at r0, the
+ * Fig. 1 observables). Asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * n = 0 is a no-op. opts may be NULL (defaults).
+ * Persistent launches: a trajectory that has used opts->slice_budget attempted steps is saved to a
+ * suspend record and finished by a second kernel that gives each such trajectory a group of lanes,
+ * which runs its steps ~3x faster; results are bit-identical to the plain kernel.
+ * Concurrency: persistent launches that share the system's own scratch must not overlap; pass a
+ * distinct opts->scratch to run them concurrently.
+ */
+int ia_launch(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* out,
+              const ia_launch_opts* opts, void* stream);
+
+/*
+ * FP64 FMA throughput microbenchmark (no counterpart in the paper: it measures the roofline
+ * denominator of the integrator). Runs `blocks_per_sm` x SMs blocks of 256 threads, each thread
+ * `iters` iterations of 8 independent fused multiply-add chains, on `stream`, timed with CUDA
+ * events around the launch; synchronises the stream. *flops = 2 * 8 * iters * threads / seconds.
+ */
+int ia_fp64_peak(int32_t blocks_per_sm, int32_t iters, void* stream, double* flops);
+
+/*
+ * Test hook (no counterpart in the paper): y[i] = 1/x[i] computed as the integrator computes 1/r^2
+ * (Newton-Raphson from an FP32 seed). x, y: device arrays of n doubles, x[i] > 0. Asynchronous.
+ */
+int ia_rcp_check(const double* x, double* y, int64_t n, void* stream);
+
+/* Static description of a return code (never NULL). */
+const char* ia_error_string(int code);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int ia_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IONATOM_H */

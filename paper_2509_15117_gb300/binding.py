@@ -1,0 +1,302 @@
+"""Thin Python binding of the C ABI in ``include/ionatom.h`` (argument marshalling only).
+
+Every step of the trajectory computation runs in the CUDA library; this module only builds the C
+structs, moves arrays to structure-of-arrays device tensors (PyTorch is used for device memory and
+streams), and turns return codes into exceptions. There is no CPU fallback: if the compiled library
+or a CUDA device is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+IA_OK = 0
+IA_KERNEL_PLAIN = 0
+IA_KERNEL_PERSISTENT = 1
+
+ST_EXIT = 0
+ST_TMAX = 1 << 0
+ST_MAX_STEPS = 1 << 1
+ST_H_UNDERFLOW = 1 << 2
+ST_NONFINITE = 1 << 3
+ST_BAD_IC = 1 << 4
+ST_EXIT_OUTSIDE = 1 << 5
+ST_COMPLEX = 1 << 8
+
+EXPORTED = ("ia_system_create", "ia_system_destroy", "ia_system_count", "ia_scratch_bytes", "ia_reserve",
+            "ia_launch", "ia_fp64_peak", "ia_rcp_check", "ia_error_string", "ia_version")
+
+
+class IaError(RuntimeError):
+    pass
+
+
+class ia_system_desc(ctypes.Structure):
+    _fields_ = [
+        ("m_ion", ctypes.c_double), ("m_atom", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("De", ctypes.c_double), ("Omega", ctypes.c_double),
+        ("a", ctypes.c_double * 3), ("q", ctypes.c_double * 3),
+        ("r0", ctypes.c_double), ("t_max", ctypes.c_double), ("rtol", ctypes.c_double),
+        ("atol_pos", ctypes.c_double), ("atol_vel", ctypes.c_double), ("h_max", ctypes.c_double),
+        ("rf_sign", ctypes.c_int32), ("reserved", ctypes.c_int32), ("max_attempts", ctypes.c_int64),
+    ]
+
+
+class ia_ic_soa(ctypes.Structure):
+    _fields_ = [("y0", ctypes.c_void_p), ("phi0", ctypes.c_void_p), ("sys_id", ctypes.c_void_p),
+                ("ld", ctypes.c_int64)]
+
+
+class ia_obs_soa(ctypes.Structure):
+    _fields_ = [("theta_s", ctypes.c_void_p), ("dp", ctypes.c_void_p), ("dE_ion", ctypes.c_void_p),
+                ("t_final", ctypes.c_void_p), ("t_first_bounce", ctypes.c_void_p),
+                ("t_last_bounce", ctypes.c_void_p), ("n_bounce", ctypes.c_void_p),
+                ("status", ctypes.c_void_p), ("n_steps", ctypes.c_void_p), ("n_rej", ctypes.c_void_p),
+                ("y_final", ctypes.c_void_p), ("ld", ctypes.c_int64)]
+
+
+class ia_launch_opts(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("block", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("refill", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("regs_variant", ctypes.c_int32), ("slice_budget", ctypes.c_int32),
+                ("tail_group", ctypes.c_int32), ("tail_blocks_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("suspend_capacity", ctypes.c_int64),
+                ("scratch", ctypes.c_void_p), ("scratch_bytes", ctypes.c_int64)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the compiled library (building it in-tree first if allowed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise IaError(f"CUDA library not built: {path}")
+        _build.build()
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    L.ia_system_create.argtypes = [P(ia_system_desc), ctypes.c_int32, P(ctypes.c_void_p)]
+    L.ia_system_create.restype = ctypes.c_int
+    L.ia_system_destroy.argtypes = [ctypes.c_void_p]
+    L.ia_system_destroy.restype = ctypes.c_int
+    L.ia_system_count.argtypes = [ctypes.c_void_p]
+    L.ia_system_count.restype = ctypes.c_int
+    L.ia_launch.argtypes = [ctypes.c_void_p, P(ia_ic_soa), ctypes.c_int64, P(ia_obs_soa),
+                            P(ia_launch_opts), ctypes.c_void_p]
+    L.ia_launch.restype = ctypes.c_int
+    L.ia_scratch_bytes.argtypes = [ctypes.c_int64, P(ia_launch_opts)]
+    L.ia_scratch_bytes.restype = ctypes.c_int64
+    L.ia_reserve.argtypes = [ctypes.c_void_p, ctypes.c_int64, P(ia_launch_opts)]
+    L.ia_reserve.restype = ctypes.c_int
+    L.ia_rcp_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    L.ia_rcp_check.restype = ctypes.c_int
+    L.ia_fp64_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, P(ctypes.c_double)]
+    L.ia_fp64_peak.restype = ctypes.c_int
+    L.ia_error_string.argtypes = [ctypes.c_int]
+    L.ia_error_string.restype = ctypes.c_char_p
+    L.ia_version.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(code: int):
+    if code != IA_OK:
+        raise IaError(f"{load().ia_error_string(code).decode()} ({code})")
+
+
+def make_desc(d: dict) -> ia_system_desc:
+    s = ia_system_desc()
+    for k in ("m_ion", "m_atom", "alpha", "De", "Omega", "r0", "t_max", "rtol", "atol_pos", "atol_vel",
+              "h_max"):
+        setattr(s, k, float(d[k]))
+    for j in range(3):
+        s.a[j] = float(d["a"][j])
+        s.q[j] = float(d["q"][j])
+    s.rf_sign = int(d.get("rf_sign", 1))
+    s.reserved = 0
+    s.max_attempts = int(d.get("max_attempts", 50_000_000))
+    return s
+
+
+def ia_system_create(systems) -> int:
+    """Create a device table from a list of descriptor dicts; returns the opaque handle."""
+    L = load()
+    arr = (ia_system_desc * len(systems))(*[make_desc(d) for d in systems])
+    h = ctypes.c_void_p()
+    _check(L.ia_system_create(arr, len(systems), ctypes.byref(h)))
+    return h.value
+
+
+def ia_system_destroy(handle: int) -> None:
+    _check(load().ia_system_destroy(handle))
+
+
+def ia_system_count(handle: int) -> int:
+    n = load().ia_system_count(handle)
+    if n < 0:
+        _check(n)
+    return n
+
+
+def ia_fp64_peak(blocks_per_sm: int = 4, iters: int = 20000, stream=None) -> float:
+    out = ctypes.c_double()
+    _check(load().ia_fp64_peak(blocks_per_sm, iters, _stream_ptr(stream), ctypes.byref(out)))
+    return out.value
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+OBS_FIELDS = ("theta_s", "dp", "dE_ion", "t_final", "t_first_bounce", "t_last_bounce", "n_bounce",
+              "status", "n_steps", "n_rej")
+
+
+def alloc_obs(n: int, device="cuda", y_final: bool = False) -> dict:
+    """Device output tensors for n trajectories (torch owns them)."""
+    import torch
+    out = {}
+    for f in ("theta_s", "dp", "dE_ion", "t_final", "t_first_bounce", "t_last_bounce"):
+        out[f] = torch.empty(n, dtype=torch.float64, device=device)
+    out["n_bounce"] = torch.empty(n, dtype=torch.int32, device=device)
+    out["status"] = torch.empty(n, dtype=torch.int32, device=device)  # bit pattern of uint32
+    out["n_steps"] = torch.empty(n, dtype=torch.int32, device=device)
+    out["n_rej"] = torch.empty(n, dtype=torch.int32, device=device)
+    if y_final:
+        out["y_final"] = torch.empty((12, n), dtype=torch.float64, device=device)
+    return out
+
+
+def _obs_struct(out: dict, n: int) -> ia_obs_soa:
+    o = ia_obs_soa()
+    for f in OBS_FIELDS:
+        setattr(o, f, out[f].data_ptr())
+    yf = out.get("y_final")
+    o.y_final = yf.data_ptr() if yf is not None else None
+    o.ld = n if yf is not None else 0
+    return o
+
+
+def to_device_soa(y0, phi0, sys_id=None, device="cuda"):
+    """(n, 12) state and (n,) phases (numpy or torch) -> SoA device tensors."""
+    import torch
+    y0 = torch.as_tensor(np.ascontiguousarray(y0) if isinstance(y0, np.ndarray) else y0, dtype=torch.float64)
+    y0_soa = y0.to(device).t().contiguous()
+    ph = torch.as_tensor(phi0, dtype=torch.float64).to(device).contiguous()
+    sid = None
+    if sys_id is not None:
+        sid = torch.as_tensor(sys_id, dtype=torch.int32).to(device).contiguous()
+    return y0_soa, ph, sid
+
+
+def make_opts(kernel: int = IA_KERNEL_PERSISTENT, block: int = 0, grid: int = 0, refill: int = 0,
+              blocks_per_sm: int = 0, regs_variant: int = 0, slice_budget: int = 0, tail_group: int = 0,
+              tail_blocks_per_sm: int = 0, suspend_capacity: int = 0, scratch=None) -> ia_launch_opts:
+    opts = ia_launch_opts()
+    opts.kernel = kernel
+    opts.block = block
+    opts.grid = grid
+    opts.refill = refill
+    opts.blocks_per_sm = blocks_per_sm
+    opts.regs_variant = regs_variant
+    opts.slice_budget = slice_budget
+    opts.tail_group = tail_group
+    opts.tail_blocks_per_sm = tail_blocks_per_sm
+    opts.suspend_capacity = suspend_capacity
+    if scratch is not None:
+        opts.scratch = scratch.data_ptr()
+        opts.scratch_bytes = scratch.numel() * scratch.element_size()
+    return opts
+
+
+def ia_scratch_bytes(n: int, **kw) -> int:
+    v = load().ia_scratch_bytes(n, ctypes.byref(make_opts(**kw)))
+    if v < 0:
+        _check(int(v))
+    return int(v)
+
+
+def ia_reserve(handle: int, n: int, **kw) -> None:
+    _check(load().ia_reserve(handle, n, ctypes.byref(make_opts(**kw))))
+
+
+def ia_rcp_check(x, y, stream=None) -> None:
+    _check(load().ia_rcp_check(x.data_ptr(), y.data_ptr(), int(x.numel()), _stream_ptr(stream)))
+
+
+def ia_launch(handle: int, y0_soa, phi0, sys_id, out: dict, kernel: int = IA_KERNEL_PERSISTENT,
+              stream=None, **kw) -> None:
+    """Launch on device tensors: y0_soa (12, n) float64, phi0 (n,), sys_id (n,) int32 or None.
+    Keyword options are the fields of ia_launch_opts (see make_opts)."""
+    n = int(phi0.shape[0])
+    ic = ia_ic_soa()
+    ic.y0 = y0_soa.data_ptr()
+    ic.phi0 = phi0.data_ptr()
+    ic.sys_id = sys_id.data_ptr() if sys_id is not None else None
+    ic.ld = int(y0_soa.stride(0)) if n > 0 else 0
+    o = _obs_struct(out, n)
+    opts = make_opts(kernel=kernel, **kw)
+    _check(load().ia_launch(handle, ctypes.byref(ic), n, ctypes.byref(o), ctypes.byref(opts),
+                            _stream_ptr(stream)))
+
+
+class System:
+    """Owns an ia_system handle (device parameter table)."""
+
+    def __init__(self, systems):
+        self.systems = [dict(s) for s in systems]
+        self.handle = ia_system_create(self.systems)
+
+    def close(self):
+        if self.handle:
+            ia_system_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, y0, phi0, sys_id=None, kernel: int = IA_KERNEL_PERSISTENT, y_final: bool = False,
+            **launch_kw) -> dict:
+        """Integrate a batch given on the host or device; returns device tensors (synchronised)."""
+        import torch
+        y0_soa, ph, sid = to_device_soa(y0, phi0, sys_id)
+        n = int(ph.shape[0])
+        out = alloc_obs(n, y_final=y_final)
+        ia_launch(self.handle, y0_soa, ph, sid, out, kernel=kernel, **launch_kw)
+        torch.cuda.synchronize()
+        return out
+
+
+def to_numpy(out: dict) -> dict:
+    r = {}
+    for k, v in out.items():
+        a = v.cpu().numpy()
+        if k == "status":
+            a = a.view(np.uint32)
+        if k == "y_final":
+            a = a.T.copy()
+        r[k] = a
+    return r

@@ -1,0 +1,52 @@
+"""In-tree build of the CUDA library ``_lib/libionatom.so`` for sm_103a (GB300).
+
+One translation unit, one ``-gencode``: nvcc cross-compiles it on a machine without a GPU as well.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+LIBDIR = os.path.join(HERE, "_lib")
+LIB = os.path.join(LIBDIR, "libionatom.so")
+SOURCES = [os.path.join(CSRC, "ia_capi.cu")]
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("ia_traj.cuh", "dp5_nystrom.h")] + [
+    os.path.join(ROOT, "include", "ionatom.h")]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-shared", *ARCH]
+
+_lock = threading.Lock()
+
+
+def nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if cand and (os.path.sep not in cand or os.path.exists(cand)):
+            return cand
+    return "nvcc"
+
+
+def up_to_date() -> bool:
+    if not os.path.exists(LIB):
+        return False
+    t = os.path.getmtime(LIB)
+    return all(os.path.getmtime(p) <= t for p in DEPS)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the library if it is missing or older than its sources; returns its path."""
+    with _lock:
+        if not force and up_to_date():
+            return LIB
+        os.makedirs(LIBDIR, exist_ok=True)
+        tmp = LIB + f".tmp{os.getpid()}"
+        cmd = [nvcc(), *NVCC_FLAGS, "-o", tmp, *SOURCES]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+            print(" ".join(cmd))
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, LIB)
+        return LIB

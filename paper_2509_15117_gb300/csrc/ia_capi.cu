@@ -1,0 +1,660 @@
+// ia_capi.cu -- kernels and the C ABI (include/ionatom.h) of the ion-atom trajectory engine.
+//
+// Kernels:
+//   k_plain       one thread per trajectory; a warp runs until its longest trajectory ends.
+//   k_persistent  a resident grid of lanes; a lane that finishes stores its observables and, once
+//                 `refill` lanes of its warp are idle, the warp claims that many new indices with one
+//                 atomic add on a 64-bit work counter. A trajectory that has used `budget` attempted
+//                 steps is saved to a suspend record and its lane takes new work: trajectory lengths
+//                 span 10^3 .. 10^7 steps (single passes against long-lived complexes).
+//   k_tail<G>     finishes the suspended trajectories, one per group of G lanes (group mode: about a
+//                 third of the FP64 instructions per step of one lane), so the longest complexes,
+//                 which bound the batch time, run ~3x faster per step.
+//   k_fp64_fma    FP64 FMA throughput microbenchmark: the denominator of the integrator's roofline.
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <new>
+#include <cuda_runtime.h>
+
+#include "ia_traj.cuh"
+#include "../../include/ionatom.h"
+
+using namespace ia;
+
+namespace {
+
+// Work counters at the start of the scratch area.
+struct Counters {
+    unsigned long long work;      // next trajectory index for k_persistent
+    unsigned long long n_susp;    // suspend records claimed
+    unsigned long long tail;      // next suspend record for k_tail
+    unsigned long long pad[5];
+};
+constexpr size_t SCRATCH_HEAD = 256;  // counters, padded so the records start 256-byte aligned
+
+__device__ __forceinline__ void store_bad_sid(const IcPtrs& ic, const ObsPtrs& out, const SysDev* tab, long long i)
+{
+    Final fin;
+    Scal S;
+    S.phi0 = 0.0;
+    S.t_first = S.t_last = 0.0;
+    S.n_acc = S.n_rej = S.n_bounce = 0;
+    const double* y = ic.y0 + i;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        fin.xi[j] = y[(0 + j) * ic.ld]; fin.vi[j] = y[(3 + j) * ic.ld];
+        fin.xa[j] = y[(6 + j) * ic.ld]; fin.va[j] = y[(9 + j) * ic.ld];
+    }
+    fin.t = 0.0;
+    fin.status = ST_BAD_IC;
+    store_result(tab[0], ic, out, i, S, fin, false);
+}
+
+__global__ void __launch_bounds__(128) k_plain(const SysDev* __restrict__ tab, int n_sys, IcPtrs ic,
+                                               ObsPtrs out, long long n)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int sid = ic.sys_id ? __ldg(ic.sys_id + i) : 0;
+    if (sid < 0 || sid >= n_sys) {
+        store_bad_sid(ic, out, tab, i);
+        return;
+    }
+    const SysDev& P = tab[sid];
+    Lane L;
+    Final fin;
+    if (!lane_init(P, ic, i, L, fin)) {
+        store_result(P, ic, out, i, L.s, fin, false);
+        return;
+    }
+    while (lane_attempt(P, L, fin) == RUNNING) {
+    }
+    store_result(P, ic, out, i, L.s, fin, true);
+}
+
+// Persistent lane-mode kernel: each lane holds one trajectory at a time.
+template <int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_persistent(const SysDev* __restrict__ tab, int n_sys, IcPtrs ic,
+                                                            ObsPtrs out, long long n, Counters* __restrict__ ctr,
+                                                            Susp* __restrict__ susp, long long cap, int refill,
+                                                            int budget)
+{
+    const int lane = threadIdx.x & 31;
+    Lane L;
+    Final fin;
+    long long my = -1;     // trajectory index held by this lane, -1 = idle
+    int sid = 0;
+    bool can_suspend = false;
+    bool drained = false;  // the queue has been seen empty by this warp
+    for (;;) {
+        const unsigned idle = __ballot_sync(FULL, my < 0);
+        const int n_idle = __popc(idle);
+        if (!drained && (n_idle >= refill || n_idle == 32)) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&ctr->work, (unsigned long long)n_idle);
+            base = __shfl_sync(FULL, base, 0);
+            if (base + (unsigned long long)n_idle >= (unsigned long long)n) drained = true;
+            if (my < 0) {
+                const int rank = __popc(idle & ((1u << lane) - 1u));
+                const unsigned long long cand = base + (unsigned long long)rank;
+                if (cand < (unsigned long long)n) {
+                    my = (long long)cand;
+                    sid = ic.sys_id ? __ldg(ic.sys_id + my) : 0;
+                    if (sid < 0 || sid >= n_sys) {
+                        store_bad_sid(ic, out, tab, my);
+                        my = -1;
+                    } else if (!lane_init(tab[sid], ic, my, L, fin)) {
+                        store_result(tab[sid], ic, out, my, L.s, fin, false);
+                        my = -1;
+                    } else {
+                        can_suspend = budget > 0;
+                    }
+                }
+            }
+        }
+        if (__ballot_sync(FULL, my >= 0) == 0) {
+            if (drained) break;
+            continue;
+        }
+        if (my >= 0) {
+            const SysDev& P = tab[sid];
+            if (lane_attempt(P, L, fin) == FINISHED) {
+                store_result(P, ic, out, my, L.s, fin, true);
+                my = -1;
+            } else if (can_suspend && !L.s.retry && L.s.n_acc + L.s.n_rej >= budget) {
+                const unsigned long long slot = atomicAdd(&ctr->n_susp, 1ull);
+                if (slot < (unsigned long long)cap) {
+                    lane_suspend(L, my, sid, susp + slot);
+                    my = -1;
+                } else {
+                    can_suspend = false;  // no room: this lane finishes the trajectory itself
+                }
+            }
+        }
+    }
+}
+
+// Group-mode kernel for suspended trajectories: one trajectory per group of G lanes.
+template <int G>
+__global__ void __launch_bounds__(128) k_tail(const SysDev* __restrict__ tab, IcPtrs ic, ObsPtrs out,
+                                              const Susp* __restrict__ susp, Counters* __restrict__ ctr,
+                                              long long cap)
+{
+    constexpr int R = (N_COEF + G - 1) / G;  // coefficient rounds per lane
+    const GroupLane<G> gl = group_lane<G>();
+    const unsigned long long n_susp_raw = *(volatile unsigned long long*)&ctr->n_susp;
+    const unsigned long long n_susp = n_susp_raw < (unsigned long long)cap ? n_susp_raw : (unsigned long long)cap;
+    double x = 0.0, v = 0.0, a1 = 0.0;
+    Scal S;
+    S.t = 0.0; S.h = 0.0; S.hmin = 0.0; S.phi0 = 0.0; S.rdot_prev = 0.0; S.t_first = 0.0; S.t_last = 0.0;
+    S.n_acc = 0; S.n_rej = 0; S.n_bounce = 0; S.nofailed = true; S.retry = false;
+    long long idx = -1;
+    int sid = 0;
+    bool active = false, drained = false;
+    for (;;) {
+        const bool need = !active && !drained;
+        if (__any_sync(FULL, need)) {
+            unsigned long long k = 0;
+            if (need && gl.c == 0) k = atomicAdd(&ctr->tail, 1ull);
+            k = __shfl_sync(FULL, k, gl.base);
+            if (need) {
+                if (k < n_susp) {
+                    const Susp* r = susp + k;
+                    x = r->x[gl.comp];
+                    v = r->v[gl.comp];
+                    a1 = r->a1[gl.comp];
+                    S.t = r->t; S.h = r->h; S.phi0 = r->phi0; S.rdot_prev = r->rdot_prev;
+                    S.t_first = r->t_first; S.t_last = r->t_last;
+                    S.n_acc = r->n_acc; S.n_rej = r->n_rej; S.n_bounce = r->n_bounce;
+                    S.nofailed = (r->flags & 1) != 0;
+                    S.retry = (r->flags & 2) != 0;
+                    S.hmin = hmin_at(S.t);
+                    idx = r->idx;
+                    sid = r->sid;
+                    active = true;
+                } else {
+                    drained = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, active)) break;
+
+        const SysDev& P = tab[sid];
+        uint32_t st = 0xffffffffu;
+        if (active) st = attempt_begin(P, S);
+        const double h = S.h, t = S.t;
+
+        // step coefficients, spread over the group's lanes
+        Coef K;
+        K.h2 = h * h;
+        double cv[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = r * G + (gl.c < G ? gl.c : 0);
+            const int kk = k < N_COEF ? k : N_COEF - 1;
+            cv[r] = COEF_K[kk] * (COEF_H2[kk] ? K.h2 : h);
+        }
+        {
+            double* kp = &K.c2;
+#pragma unroll
+            for (int k = 0; k < N_COEF; ++k) kp[k] = shfl(cv[k / G], gl.base + (k % G));
+        }
+        // rf phases of stages 2..6 (stage 7 shares stage 6's time), one per lane
+        const double chsel = gl.c < 4 ? cv[0] : h;
+        const double cl = cos(fma(P.Omega, t + chsel, S.phi0));
+        const double cs2 = shfl(cl, gl.base + 0), cs3 = shfl(cl, gl.base + 1), cs4 = shfl(cl, gl.base + 2);
+        const double cs5 = shfl(cl, gl.base + 3), cs67 = shfl(cl, gl.base + 4);
+
+        const double kq = gl.comp < 3 ? P.kq[gl.comp] : 0.0;
+        const double ka = gl.comp < 3 ? P.ka[gl.comp] : 0.0;
+        double r2, d3[3];
+        const double a2 = accel_group<G>(P, gl, pos2(K, x, v), cs2, kq, ka, r2, d3);
+        const double a3 = accel_group<G>(P, gl, pos3(K, x, v, a1), cs3, kq, ka, r2, d3);
+        const double a4 = accel_group<G>(P, gl, pos4(K, x, v, a1, a2), cs4, kq, ka, r2, d3);
+        const double a5 = accel_group<G>(P, gl, pos5(K, x, v, a1, a2, a3), cs5, kq, ka, r2, d3);
+        const double a6 = accel_group<G>(P, gl, pos6(K, h, x, v, a1, a2, a3, a4), cs67, kq, ka, r2, d3);
+        const double xn = pos7(K, h, x, v, a1, a3, a4, a5);
+        double r2new, dn[3];
+        const double a7 = accel_group<G>(P, gl, xn, cs67, kq, ka, r2new, dn);
+        const double vn = vel_new(K, v, a1, a3, a4, a5, a6);
+
+        bool okx, fx, okv, fv;
+        float rx, rv;
+        err_check(P.rtol, P.atol_pos, x, xn, err_x(K, a1, a3, a4, a5, a6), okx, fx, rx);
+        err_check(P.rtol, P.atol_vel, v, vn, err_v(K, a1, a3, a4, a5, a6, a7), okv, fv, rv);
+        const bool real = gl.c < 6;
+        const bool ok = !real || (okx && okv);
+        const bool fi = !real || (fx && fv);
+        const float ratio = real ? fmaxf(rx, rv) : 0.0f;
+        const unsigned gmask = ((1u << G) - 1u) << gl.base;
+        const bool accept = (__ballot_sync(FULL, !ok) & gmask) == 0;
+        const bool finite = (__ballot_sync(FULL, !fi) & gmask) == 0;
+        float errf = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) errf = fmaxf(errf, __shfl_sync(FULL, ratio, gl.base + k));
+        // radial velocity sign at the step end: d . (v_a - v_i)
+        const int j = gl.comp < 3 ? gl.comp : gl.comp - 3;
+        const double wj = shfl(vn, gl.base + 3 + j) - shfl(vn, gl.base + j);
+        const double w0 = shfl(wj, gl.base + 0), w1 = shfl(wj, gl.base + 1), w2 = shfl(wj, gl.base + 2);
+        const double rd = fma(dn[0], w0, fma(dn[1], w1, dn[2] * w2));
+
+        int res = 0;  // 0 running, 1 stopped, 2 exits in this step
+        if (active) {
+            if (st != 0xffffffffu) {
+                res = 1;
+            } else if (!finite) {
+                res = 1;
+                st = ST_NONFINITE;
+            } else if (!accept) {
+                st = on_reject(P, S, errf);
+                if (st != 0xffffffffu) res = 1;
+            } else if (on_accept(P, S, rd, r2new)) {
+                res = 2;
+            } else {
+                x = xn;
+                v = vn;
+                a1 = a7;
+                on_commit(P, S, errf);
+            }
+        }
+        if (__any_sync(FULL, res != 0)) {
+            Final fin;
+            fin.t = S.t;
+            fin.status = st;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                fin.xi[k] = shfl(x, gl.base + k);
+                fin.xa[k] = shfl(x, gl.base + 3 + k);
+                fin.vi[k] = shfl(v, gl.base + k);
+                fin.va[k] = shfl(v, gl.base + 3 + k);
+            }
+            if (__any_sync(FULL, res == 2)) {
+                StepData D;
+                double xni[3], xna[3], vni[3], vna[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    D.xi[k] = fin.xi[k]; D.xa[k] = fin.xa[k]; D.vi[k] = fin.vi[k]; D.va[k] = fin.va[k];
+                    D.a1i[k] = shfl(a1, gl.base + k); D.a1a[k] = shfl(a1, gl.base + 3 + k);
+                    D.a3i[k] = shfl(a3, gl.base + k); D.a3a[k] = shfl(a3, gl.base + 3 + k);
+                    D.a4i[k] = shfl(a4, gl.base + k); D.a4a[k] = shfl(a4, gl.base + 3 + k);
+                    D.a5i[k] = shfl(a5, gl.base + k); D.a5a[k] = shfl(a5, gl.base + 3 + k);
+                    D.a6i[k] = shfl(a6, gl.base + k); D.a6a[k] = shfl(a6, gl.base + 3 + k);
+                    D.a7i[k] = shfl(a7, gl.base + k); D.a7a[k] = shfl(a7, gl.base + 3 + k);
+                    xni[k] = shfl(xn, gl.base + k); xna[k] = shfl(xn, gl.base + 3 + k);
+                    vni[k] = shfl(vn, gl.base + k); vna[k] = shfl(vn, gl.base + 3 + k);
+                }
+                D.h = h;
+                D.t = t;
+                if (res == 2 && gl.c == 0) finish_exit(P, D, xni, xna, vni, vna, r2new, fin);
+            }
+            if (res != 0) {
+                if (gl.c == 0) store_result(P, ic, out, idx, S, fin, true);
+                active = false;
+            }
+        }
+    }
+}
+
+__global__ void k_fp64_fma(double* out, int iters, double a, double b)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double x0 = 1.0 + 1e-9 * (double)g, x1 = x0 + 1e-3, x2 = x0 + 2e-3, x3 = x0 + 3e-3;
+    double x4 = x0 + 4e-3, x5 = x0 + 5e-3, x6 = x0 + 6e-3, x7 = x0 + 7e-3;
+    for (int i = 0; i < iters; ++i) {
+        x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+        x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    }
+    out[g] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+}
+
+__global__ void k_rcp_check(const double* x, double* y, long long n)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = rcp_nr(x[i]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Host side
+
+struct ia_system {
+    int device;
+    int n_sys;
+    SysDev* d_tab;
+    void* d_scratch;          // library-owned scratch (grown on demand)
+    size_t scratch_bytes;
+    int num_sms;
+};
+
+namespace {
+
+bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+bool valid_desc(const ia_system_desc& d)
+{
+    auto pos = [](double x) { return std::isfinite(x) && x > 0.0; };
+    if (!pos(d.m_ion) || !pos(d.m_atom) || !pos(d.Omega) || !pos(d.r0) || !pos(d.t_max)) return false;
+    if (!pos(d.rtol) || !pos(d.atol_pos) || !pos(d.atol_vel) || !pos(d.h_max)) return false;
+    if (!std::isfinite(d.alpha) || d.alpha < 0.0) return false;
+    if (d.alpha > 0.0 && !pos(d.De)) return false;
+    for (int j = 0; j < 3; ++j)
+        if (!std::isfinite(d.a[j]) || !std::isfinite(d.q[j])) return false;
+    if (d.rf_sign != 1 && d.rf_sign != -1) return false;
+    if (d.reserved != 0 || d.max_attempts <= 0 || d.max_attempts > 0x7fffffffLL) return false;
+    return true;
+}
+
+// Constants of one system (text after Eq. 1: C4 = alpha/2, C8 = C4^2/(4 De); Eq. 1's trap term).
+SysDev derive(const ia_system_desc& d)
+{
+    SysDev P;
+    std::memset(&P, 0, sizeof(P));
+    const double C4 = 0.5 * d.alpha;
+    const double C8 = C4 > 0.0 ? C4 * C4 / (4.0 * d.De) : 0.0;
+    P.inv_mi = 1.0 / d.m_ion;
+    P.inv_ma = 1.0 / d.m_atom;
+    P.neg_inv_mi = -P.inv_mi;
+    P.c8x8 = 8.0 * C8;
+    P.c4x4 = 4.0 * C4;
+    P.Omega = d.Omega;
+    const double W2 = d.Omega * d.Omega;
+    for (int j = 0; j < 3; ++j) {
+        P.ka[j] = -(W2 / 4.0) * d.a[j];
+        P.kq[j] = -(W2 / 4.0) * (2.0 * (double)d.rf_sign * d.q[j]);
+        P.ua[j] = (d.m_ion * W2 / 8.0) * d.a[j];
+        P.uq[j] = (d.m_ion * W2 / 8.0) * (2.0 * (double)d.rf_sign * d.q[j]);
+    }
+    P.m_i = d.m_ion;
+    P.m_a = d.m_atom;
+    P.r0sq = d.r0 * d.r0;
+    P.t_max = d.t_max;
+    P.h_max = d.h_max;
+    P.rtol = d.rtol;
+    P.atol_pos = d.atol_pos;
+    P.atol_vel = d.atol_vel;
+    P.thr_pos = d.atol_pos / d.rtol;
+    P.thr_vel = d.atol_vel / d.rtol;
+    P.hinit_den = 0.8 * std::pow(d.rtol, 0.2);
+    P.max_attempts = (long long)d.max_attempts;
+    return P;
+}
+
+struct Resolved {
+    ia_launch_opts o;
+    long long cap;  // suspend records
+    size_t bytes;   // scratch bytes
+};
+
+constexpr int DEFAULT_BUDGET = 65536;
+
+int resolve(int64_t n, const ia_launch_opts* opts, Resolved& r)
+{
+    std::memset(&r.o, 0, sizeof(r.o));
+    if (opts) r.o = *opts;
+    ia_launch_opts& o = r.o;
+    if (o.kernel != IA_KERNEL_PLAIN && o.kernel != IA_KERNEL_PERSISTENT) return IA_ERR_INVALID_ARG;
+    if (o.reserved != 0) return IA_ERR_INVALID_ARG;
+    if (o.refill == 0) o.refill = 1;
+    if (o.refill < 1 || o.refill > 32) return IA_ERR_INVALID_ARG;
+    if (o.grid < 0 || o.blocks_per_sm < 0 || o.tail_blocks_per_sm < 0) return IA_ERR_INVALID_ARG;
+    if (o.slice_budget == 0) o.slice_budget = DEFAULT_BUDGET;
+    if (o.slice_budget < -1) return IA_ERR_INVALID_ARG;
+    if (o.tail_group == 0) o.tail_group = 6;
+    if (o.tail_group != 6 && o.tail_group != 8) return IA_ERR_INVALID_ARG;
+    if (o.tail_blocks_per_sm == 0) o.tail_blocks_per_sm = 1;
+    if (o.tail_blocks_per_sm > 16) return IA_ERR_INVALID_ARG;
+    if (o.regs_variant != 0 && o.regs_variant != 1 && o.regs_variant != 3) return IA_ERR_INVALID_ARG;
+    if (o.suspend_capacity < 0) return IA_ERR_INVALID_ARG;
+    r.cap = 0;
+    if (o.kernel == IA_KERNEL_PERSISTENT && o.slice_budget > 0) {
+        long long cap = o.suspend_capacity;
+        if (cap == 0) {
+            cap = n / 32;
+            if (cap < 4096) cap = 4096;
+            if (cap > n) cap = n;
+        }
+        r.cap = cap;
+    }
+    r.bytes = SCRATCH_HEAD + (size_t)r.cap * sizeof(Susp);
+    return IA_OK;
+}
+
+// Builds of the persistent kernel: (block, minimum resident blocks per SM). The register cap of
+// 3 x 128-thread blocks per SM (168 registers) is the only one that does not spill the step.
+const void* persistent_fn(int block, int minb)
+{
+    if (block == 64) return (const void*)k_persistent<64, 1>;
+    if (block == 256) return (const void*)k_persistent<256, 1>;
+    if (minb == 3) return (const void*)k_persistent<128, 3>;
+    return (const void*)k_persistent<128, 1>;
+}
+
+void launch_persistent(int block, int minb, int grid, cudaStream_t st, const SysDev* tab, int n_sys, IcPtrs icp,
+                       ObsPtrs op, long long n, Counters* ctr, Susp* susp, long long cap, int refill, int budget)
+{
+    if (block == 64)
+        k_persistent<64, 1><<<grid, 64, 0, st>>>(tab, n_sys, icp, op, n, ctr, susp, cap, refill, budget);
+    else if (block == 256)
+        k_persistent<256, 1><<<grid, 256, 0, st>>>(tab, n_sys, icp, op, n, ctr, susp, cap, refill, budget);
+    else if (minb == 3)
+        k_persistent<128, 3><<<grid, 128, 0, st>>>(tab, n_sys, icp, op, n, ctr, susp, cap, refill, budget);
+    else
+        k_persistent<128, 1><<<grid, 128, 0, st>>>(tab, n_sys, icp, op, n, ctr, susp, cap, refill, budget);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ia_version(void) { return 200; }
+
+const char* ia_error_string(int code)
+{
+    switch (code) {
+        case IA_OK: return "ok";
+        case IA_ERR_INVALID_ARG: return "invalid argument";
+        case IA_ERR_BAD_DESC: return "system descriptor fails validation";
+        case IA_ERR_CUDA: return "CUDA runtime error";
+        case IA_ERR_ALIGNMENT: return "device pointer not 8-byte aligned (scratch: 256-byte)";
+        case IA_ERR_NO_DEVICE: return "no usable CUDA device (sm_103 required)";
+        case IA_ERR_TOO_LARGE: return "size beyond a documented limit";
+        default: return "unknown error code";
+    }
+}
+
+int ia_system_create(const ia_system_desc* desc, int32_t n_sys, ia_system** out)
+{
+    if (!desc || !out || n_sys < 1 || n_sys > 65536) return IA_ERR_INVALID_ARG;
+    for (int k = 0; k < n_sys; ++k)
+        if (!valid_desc(desc[k])) return IA_ERR_BAD_DESC;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return IA_ERR_NO_DEVICE;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return IA_ERR_NO_DEVICE;
+    if (prop.major != 10 || prop.minor != 3) return IA_ERR_NO_DEVICE;
+    SysDev* host = new (std::nothrow) SysDev[n_sys];
+    if (!host) return IA_ERR_INVALID_ARG;
+    for (int k = 0; k < n_sys; ++k) host[k] = derive(desc[k]);
+    ia_system* s = new (std::nothrow) ia_system;
+    if (!s) {
+        delete[] host;
+        return IA_ERR_INVALID_ARG;
+    }
+    s->device = dev;
+    s->n_sys = n_sys;
+    s->d_tab = nullptr;
+    s->d_scratch = nullptr;
+    s->scratch_bytes = 0;
+    s->num_sms = prop.multiProcessorCount;
+    if (cudaMalloc(&s->d_tab, sizeof(SysDev) * (size_t)n_sys) != cudaSuccess ||
+        cudaMemcpy(s->d_tab, host, sizeof(SysDev) * (size_t)n_sys, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(s->d_tab);
+        delete s;
+        delete[] host;
+        return IA_ERR_CUDA;
+    }
+    delete[] host;
+    *out = s;
+    return IA_OK;
+}
+
+int ia_system_destroy(ia_system* sys)
+{
+    if (!sys) return IA_OK;
+    cudaFree(sys->d_tab);
+    cudaFree(sys->d_scratch);
+    delete sys;
+    return IA_OK;
+}
+
+int ia_system_count(const ia_system* sys)
+{
+    if (!sys) return IA_ERR_INVALID_ARG;
+    return sys->n_sys;
+}
+
+int64_t ia_scratch_bytes(int64_t n, const ia_launch_opts* opts)
+{
+    if (n < 0) return IA_ERR_INVALID_ARG;
+    Resolved r;
+    int rc = resolve(n, opts, r);
+    if (rc != IA_OK) return rc;
+    return (int64_t)r.bytes;
+}
+
+int ia_reserve(ia_system* sys, int64_t n, const ia_launch_opts* opts)
+{
+    if (!sys || n < 0) return IA_ERR_INVALID_ARG;
+    Resolved r;
+    int rc = resolve(n, opts, r);
+    if (rc != IA_OK) return rc;
+    if (r.bytes <= sys->scratch_bytes) return IA_OK;
+    void* p = nullptr;
+    if (cudaMalloc(&p, r.bytes) != cudaSuccess) return IA_ERR_CUDA;
+    cudaFree(sys->d_scratch);
+    sys->d_scratch = p;
+    sys->scratch_bytes = r.bytes;
+    return IA_OK;
+}
+
+int ia_launch(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* out,
+              const ia_launch_opts* opts, void* stream)
+{
+    if (!sys || !ic || !out || n < 0) return IA_ERR_INVALID_ARG;
+    if (n == 0) return IA_OK;
+    if (!ic->y0 || !ic->phi0 || ic->ld < n) return IA_ERR_INVALID_ARG;
+    if (!out->theta_s || !out->dp || !out->dE_ion || !out->t_final || !out->t_first_bounce ||
+        !out->t_last_bounce || !out->n_bounce || !out->status || !out->n_steps || !out->n_rej)
+        return IA_ERR_INVALID_ARG;
+    if (out->y_final && out->ld < n) return IA_ERR_INVALID_ARG;
+    if (!aligned8(ic->y0) || !aligned8(ic->phi0) || !aligned8(out->theta_s) || !aligned8(out->dp) ||
+        !aligned8(out->dE_ion) || !aligned8(out->t_final) || !aligned8(out->t_first_bounce) ||
+        !aligned8(out->t_last_bounce) || (out->y_final && !aligned8(out->y_final)))
+        return IA_ERR_ALIGNMENT;
+    Resolved r;
+    int rc = resolve(n, opts, r);
+    if (rc != IA_OK) return rc;
+    const ia_launch_opts& o = r.o;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+    IcPtrs icp{ic->y0, ic->phi0, ic->sys_id, (long long)ic->ld};
+    ObsPtrs op{out->theta_s, out->dp, out->dE_ion, out->t_final, out->t_first_bounce, out->t_last_bounce,
+               out->n_bounce, out->status, out->n_steps, out->n_rej, out->y_final,
+               (long long)(out->y_final ? out->ld : 0)};
+
+    if (o.kernel == IA_KERNEL_PLAIN) {
+        if (o.block != 0 && o.block != 128) return IA_ERR_INVALID_ARG;
+        const int block = 128;
+        const long long blocks = (n + block - 1) / block;
+        if (blocks > 0x7fffffffLL) return IA_ERR_TOO_LARGE;
+        k_plain<<<(unsigned)blocks, block, 0, st>>>(sys->d_tab, sys->n_sys, icp, op, (long long)n);
+        return cudaGetLastError() == cudaSuccess ? IA_OK : IA_ERR_CUDA;
+    }
+
+    // scratch: caller's, else the system's own (grown here if needed: not inside a stream capture)
+    char* scratch = nullptr;
+    if (o.scratch) {
+        if ((size_t)o.scratch_bytes < r.bytes) return IA_ERR_TOO_LARGE;
+        if ((reinterpret_cast<uintptr_t>(o.scratch) & 255u) != 0) return IA_ERR_ALIGNMENT;
+        scratch = static_cast<char*>(o.scratch);
+    } else {
+        rc = ia_reserve(sys, n, opts);
+        if (rc != IA_OK) return rc;
+        scratch = static_cast<char*>(sys->d_scratch);
+    }
+    Counters* ctr = reinterpret_cast<Counters*>(scratch);
+    Susp* susp = reinterpret_cast<Susp*>(scratch + SCRATCH_HEAD);
+
+    const int block = o.block == 0 ? 128 : o.block;
+    if (block != 64 && block != 128 && block != 256) return IA_ERR_INVALID_ARG;
+    if (o.regs_variant != 0 && o.regs_variant != 1 && !(o.regs_variant == 3 && block == 128))
+        return IA_ERR_INVALID_ARG;
+    const int minb = o.regs_variant == 3 ? 3 : 1;
+    const void* fn = persistent_fn(block, minb);
+    int grid = o.grid;
+    if (grid == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0) != cudaSuccess || nb <= 0)
+            return IA_ERR_CUDA;
+        if (o.blocks_per_sm > 0 && o.blocks_per_sm < nb) nb = o.blocks_per_sm;
+        grid = nb * sys->num_sms;
+    }
+    if (cudaMemsetAsync(ctr, 0, sizeof(Counters), st) != cudaSuccess) return IA_ERR_CUDA;
+    const int budget = o.slice_budget > 0 ? o.slice_budget : 0;
+    launch_persistent(block, minb, grid, st, sys->d_tab, sys->n_sys, icp, op, n, ctr, susp, r.cap, o.refill, budget);
+    if (cudaGetLastError() != cudaSuccess) return IA_ERR_CUDA;
+    if (budget > 0) {
+        const int tgrid = o.tail_blocks_per_sm * sys->num_sms;
+        if (o.tail_group == 8)
+            k_tail<8><<<tgrid, 128, 0, st>>>(sys->d_tab, icp, op, susp, ctr, r.cap);
+        else
+            k_tail<6><<<tgrid, 128, 0, st>>>(sys->d_tab, icp, op, susp, ctr, r.cap);
+        if (cudaGetLastError() != cudaSuccess) return IA_ERR_CUDA;
+    }
+    return IA_OK;
+}
+
+int ia_rcp_check(const double* x, double* y, int64_t n, void* stream)
+{
+    if (!x || !y || n < 0) return IA_ERR_INVALID_ARG;
+    if (n == 0) return IA_OK;
+    const long long blocks = (n + 255) / 256;
+    k_rcp_check<<<(unsigned)blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, y, (long long)n);
+    return cudaGetLastError() == cudaSuccess ? IA_OK : IA_ERR_CUDA;
+}
+
+int ia_fp64_peak(int32_t blocks_per_sm, int32_t iters, void* stream, double* flops)
+{
+    if (!flops || blocks_per_sm < 1 || blocks_per_sm > 64 || iters < 1) return IA_ERR_INVALID_ARG;
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+        return IA_ERR_NO_DEVICE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int block = 256;
+    const int grid = blocks_per_sm * prop.multiProcessorCount;
+    double* buf = nullptr;
+    if (cudaMalloc(&buf, sizeof(double) * (size_t)grid * block) != cudaSuccess) return IA_ERR_CUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_fp64_fma<<<grid, block, 0, st>>>(buf, 16, 0.999999, 1e-6);  // warm-up
+    cudaEventRecord(e0, st);
+    k_fp64_fma<<<grid, block, 0, st>>>(buf, iters, 0.999999, 1e-6);
+    cudaEventRecord(e1, st);
+    int rc = IA_OK;
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = IA_ERR_CUDA;
+    float ms = 0.0f;
+    if (rc == IA_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = IA_ERR_CUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (rc != IA_OK) return rc;
+    *flops = 2.0 * 8.0 * (double)iters * (double)grid * (double)block / (1e-3 * (double)ms);
+    return IA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function include/ionatom.h declares.
+No compute call is made here (no GPU on the build machine)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2509_15117_gb300 import binding as Bd
+from paper_2509_15117_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*(ia_[a-z0-9_]+)\s*\(",
+                            text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("ia_system_create", "ia_system_destroy", "ia_launch", "ia_error_string"):
+        assert required in names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = B.build()
+    lib = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    for name in Bd.EXPORTED:
+        assert hasattr(lib, name), name
+
+
+def test_error_strings_and_version_without_gpu():
+    L = Bd.load()
+    assert L.ia_version() >= 100
+    for code in (0, -1, -2, -3, -4, -5, -6, -99):
+        assert L.ia_error_string(code)
+
+
+def test_struct_layouts_match_header():
+    # sizes of the C structs as the header defines them (x86-64 / aarch64 LP64)
+    assert ctypes.sizeof(Bd.ia_system_desc) == 8 * 17 + 4 * 2 + 8
+    assert ctypes.sizeof(Bd.ia_ic_soa) == 8 * 4
+    assert ctypes.sizeof(Bd.ia_obs_soa) == 8 * 12
+    assert ctypes.sizeof(Bd.ia_launch_opts) == 4 * 10 + 8 * 3
+
+
+def test_invalid_arguments_rejected_without_touching_gpu():
+    L = Bd.load()
+    # NULL handle / arguments are rejected before any CUDA call
+    assert L.ia_launch(None, None, 0, None, None, None) == -1
+    assert L.ia_system_create(None, 1, None) == -1
+    assert L.ia_system_count(None) == -1
+    assert L.ia_system_destroy(None) == 0
+    # scratch sizing is pure host arithmetic
+    assert Bd.ia_scratch_bytes(0) == 256
+    assert Bd.ia_scratch_bytes(100000, kernel=Bd.IA_KERNEL_PERSISTENT) == 256 + 256 * 4096
+    assert Bd.ia_scratch_bytes(1 << 20, kernel=Bd.IA_KERNEL_PERSISTENT) == 256 + 256 * (1 << 15)
+    assert Bd.ia_scratch_bytes(1000, kernel=Bd.IA_KERNEL_PERSISTENT, slice_budget=-1) == 256
+    with pytest.raises(Bd.IaError):
+        Bd.ia_scratch_bytes(10, kernel=Bd.IA_KERNEL_PERSISTENT, tail_group=5)
