@@ -66,7 +66,9 @@ def parse():
 
 def profile_case():
     """Small fixed case for ncu captures: 4096 head-on Rb trajectories at 1 mK on a 64 x 64 octant grid
-    (short, single-bounce dominated), run once by the persistent kernel and once by the plain kernel."""
+    (short, single-bounce dominated), run by the persistent kernel (default budget: its tail kernel
+    gets no work), by the persistent kernel with a 300-step budget (the tail kernel finishes almost
+    every trajectory) and by the plain kernel."""
     import torch
     from paper_2509_15117_gb300 import binding as Bd
     systems = I.c2_systems()
@@ -75,8 +77,9 @@ def profile_case():
     v0 = I.speed_for_energy(I.kelvin(I.C2_ENERGIES_K[-1]), rb_hot.m_atom)
     y0 = I.head_on(th, ph, rb_hot.r0, v0)
     with Bd.System([rb_hot.as_dict()]) as S:
-        for kernel in (Bd.IA_KERNEL_PERSISTENT, Bd.IA_KERNEL_PLAIN):
-            out = S.run(y0, np.zeros(len(y0)), None, kernel=kernel)
+        for kernel, kw in ((Bd.IA_KERNEL_PERSISTENT, {}), (Bd.IA_KERNEL_PERSISTENT, {"slice_budget": 300}),
+                           (Bd.IA_KERNEL_PLAIN, {})):
+            out = S.run(y0, np.zeros(len(y0)), None, kernel=kernel, **kw)
     torch.cuda.synchronize()
     n = int(out["n_steps"].sum().item() + out["n_rej"].sum().item())
     print(json.dumps({"profile_case": "Rb 1 mK head-on 64x64", "trajectories": len(y0), "attempted_steps": n}))
