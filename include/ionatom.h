@@ -166,6 +166,30 @@ int ia_launch(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* 
               const ia_launch_opts* opts, void* stream);
 
 /*
+ * Allocation-free variant of the persistent launch (no counterpart in the paper; it exists for
+ * callers that cannot allocate device memory when they launch: code recording a CUDA graph, where
+ * cudaMalloc is not allowed during capture; plug-ins inside a host program that owns all device
+ * memory through its own pool; real-time loops that forbid allocation after start-up).
+ *
+ * Same arguments, results and asynchrony as ia_launch with opts->kernel = IA_KERNEL_PERSISTENT
+ * (required; opts->scratch must be NULL and scratch_bytes 0). Its scratch is a fixed device array of
+ * IA_STATIC_SCRATCH_BYTES in the library, which every GPU that loads the library keeps until the
+ * process exits. It calls no cudaMalloc or cudaFree.
+ *   - Limit: ia_scratch_bytes(n, opts) must not exceed IA_STATIC_SCRATCH_BYTES (room for the counters
+ *     and 16383 suspend records); otherwise IA_ERR_TOO_LARGE and nothing runs. For large batches set
+ *     opts->suspend_capacity <= 16383 (trajectories that find no record finish in their lanes).
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ *     device current; make that first call before any stream capture. The current device must be the
+ *     one the system table was created on (else IA_ERR_INVALID_ARG).
+ *   - Every call shares the one array and leaves its contents behind; the counters it needs at zero
+ *     are cleared on the stream at the start of each call. Calls whose work overlaps on the GPU
+ *     (other streams, other host threads) race on the array: serialise them.
+ */
+#define IA_STATIC_SCRATCH_BYTES (4u << 20)
+int ia_launch_static(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* out,
+                     const ia_launch_opts* opts, void* stream);
+
+/*
  * FP64 FMA throughput microbenchmark (no counterpart in the paper: it measures the roofline
  * denominator of the integrator). Runs `blocks_per_sm` x SMs blocks of 256 threads, each thread
  * `iters` iterations of 8 independent fused multiply-add chains, on `stream`, timed with CUDA

@@ -30,7 +30,9 @@ ST_EXIT_OUTSIDE = 1 << 5
 ST_COMPLEX = 1 << 8
 
 EXPORTED = ("ia_system_create", "ia_system_destroy", "ia_system_count", "ia_scratch_bytes", "ia_reserve",
-            "ia_launch", "ia_fp64_peak", "ia_rcp_check", "ia_error_string", "ia_version")
+            "ia_launch", "ia_launch_static", "ia_fp64_peak", "ia_rcp_check", "ia_error_string", "ia_version")
+
+IA_STATIC_SCRATCH_BYTES = 4 << 20
 
 
 class IaError(RuntimeError):
@@ -95,6 +97,9 @@ def load(build_if_missing: bool = True):
     L.ia_launch.argtypes = [ctypes.c_void_p, P(ia_ic_soa), ctypes.c_int64, P(ia_obs_soa),
                             P(ia_launch_opts), ctypes.c_void_p]
     L.ia_launch.restype = ctypes.c_int
+    L.ia_launch_static.argtypes = [ctypes.c_void_p, P(ia_ic_soa), ctypes.c_int64, P(ia_obs_soa),
+                                   P(ia_launch_opts), ctypes.c_void_p]
+    L.ia_launch_static.restype = ctypes.c_int
     L.ia_scratch_bytes.argtypes = [ctypes.c_int64, P(ia_launch_opts)]
     L.ia_scratch_bytes.restype = ctypes.c_int64
     L.ia_reserve.argtypes = [ctypes.c_void_p, ctypes.c_int64, P(ia_launch_opts)]
@@ -252,6 +257,21 @@ def ia_launch(handle: int, y0_soa, phi0, sys_id, out: dict, kernel: int = IA_KER
     opts = make_opts(kernel=kernel, **kw)
     _check(load().ia_launch(handle, ctypes.byref(ic), n, ctypes.byref(o), ctypes.byref(opts),
                             _stream_ptr(stream)))
+
+
+def ia_launch_static(handle: int, y0_soa, phi0, sys_id, out: dict, stream=None, **kw) -> None:
+    """Persistent launch whose scratch is the library's fixed device array (allocates nothing).
+    Same tensors as ia_launch; keyword options as make_opts (kernel is always persistent)."""
+    n = int(phi0.shape[0])
+    ic = ia_ic_soa()
+    ic.y0 = y0_soa.data_ptr()
+    ic.phi0 = phi0.data_ptr()
+    ic.sys_id = sys_id.data_ptr() if sys_id is not None else None
+    ic.ld = int(y0_soa.stride(0)) if n > 0 else 0
+    o = _obs_struct(out, n)
+    opts = make_opts(kernel=IA_KERNEL_PERSISTENT, **kw)
+    _check(load().ia_launch_static(handle, ctypes.byref(ic), n, ctypes.byref(o), ctypes.byref(opts),
+                                   _stream_ptr(stream)))
 
 
 class System:

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <cmath>
+#include <mutex>
 #include <new>
 #include <cuda_runtime.h>
 
@@ -658,3 +659,58 @@ int ia_fp64_peak(int32_t blocks_per_sm, int32_t iters, void* stream, double* flo
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free launch: the persistent launch with its scratch in a fixed device array.
+//
+// Some callers cannot allocate device memory at the time they launch: code that records a CUDA
+// graph (cudaMalloc is not allowed during stream capture), plug-ins running inside a host program
+// that owns the whole device-memory budget through its own pool, and real-time loops that forbid
+// allocation after start-up. ia_launch_static serves them with scratch that exists from the moment
+// the library's device code is loaded on a GPU until the process exits.
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_ia_static_scratch[IA_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+
+// Device address of g_ia_static_scratch on the current device (looked up once per device).
+int static_scratch_address(int dev, void** out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return IA_ERR_NO_DEVICE;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_ia_static_scratch) != cudaSuccess || !p) return IA_ERR_CUDA;
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return IA_OK;
+}
+
+}  // namespace
+
+extern "C" int ia_launch_static(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* out,
+                                const ia_launch_opts* opts, void* stream)
+{
+    if (!sys || n < 0) return IA_ERR_INVALID_ARG;
+    ia_launch_opts o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (o.kernel != IA_KERNEL_PERSISTENT || o.scratch != nullptr || o.scratch_bytes != 0) return IA_ERR_INVALID_ARG;
+    const int64_t need = ia_scratch_bytes(n, &o);
+    if (need < 0) return (int)need;
+    if (need > (int64_t)IA_STATIC_SCRATCH_BYTES) return IA_ERR_TOO_LARGE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return IA_ERR_NO_DEVICE;
+    if (dev != sys->device) return IA_ERR_INVALID_ARG;
+    void* p = nullptr;
+    const int rc = static_scratch_address(dev, &p);
+    if (rc != IA_OK) return rc;
+    o.scratch = p;
+    o.scratch_bytes = (int64_t)IA_STATIC_SCRATCH_BYTES;
+    return ia_launch(sys, ic, n, out, &o, stream);
+}
