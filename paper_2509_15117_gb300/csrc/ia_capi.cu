@@ -38,7 +38,7 @@ constexpr size_t SCRATCH_HEAD = 256;  // counters, padded so the records start 2
 __device__ __forceinline__ void store_bad_sid(const IcPtrs& ic, const ObsPtrs& out, const SysDev* tab, long long i)
 {
     Final fin;
-    Scal S;
+    Tally S;
     S.phi0 = 0.0;
     S.t_first = S.t_last = 0.0;
     S.n_acc = S.n_rej = S.n_bounce = 0;
@@ -67,12 +67,12 @@ __global__ void __launch_bounds__(128) k_plain(const SysDev* __restrict__ tab, i
     Lane L;
     Final fin;
     if (!lane_init(P, ic, i, L, fin)) {
-        store_result(P, ic, out, i, L.s, fin, false);
+        store_result(P, ic, out, i, tally(L.s), fin, false);
         return;
     }
     while (lane_attempt(P, L, fin) == RUNNING) {
     }
-    store_result(P, ic, out, i, L.s, fin, true);
+    store_result(P, ic, out, i, tally(L.s), fin, true);
 }
 
 // Persistent lane-mode kernel: each lane holds one trajectory at a time.
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_persistent(const SysDev* __rest
                         store_bad_sid(ic, out, tab, my);
                         my = -1;
                     } else if (!lane_init(tab[sid], ic, my, L, fin)) {
-                        store_result(tab[sid], ic, out, my, L.s, fin, false);
+                        store_result(tab[sid], ic, out, my, tally(L.s), fin, false);
                         my = -1;
                     } else {
                         can_suspend = budget > 0;
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_persistent(const SysDev* __rest
         if (my >= 0) {
             const SysDev& P = tab[sid];
             if (lane_attempt(P, L, fin) == FINISHED) {
-                store_result(P, ic, out, my, L.s, fin, true);
+                store_result(P, ic, out, my, tally(L.s), fin, true);
                 my = -1;
             } else if (can_suspend && !L.s.retry && L.s.n_acc + L.s.n_rej >= budget) {
                 const unsigned long long slot = atomicAdd(&ctr->n_susp, 1ull);
@@ -273,7 +273,6 @@ __global__ void __launch_bounds__(128) k_tail(const SysDev* __restrict__ tab, Ic
             }
             if (__any_sync(FULL, res == 2)) {
                 StepData D;
-                double xni[3], xna[3], vni[3], vna[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     D.xi[k] = fin.xi[k]; D.xa[k] = fin.xa[k]; D.vi[k] = fin.vi[k]; D.va[k] = fin.va[k];
@@ -283,15 +282,15 @@ __global__ void __launch_bounds__(128) k_tail(const SysDev* __restrict__ tab, Ic
                     D.a5i[k] = shfl(a5, gl.base + k); D.a5a[k] = shfl(a5, gl.base + 3 + k);
                     D.a6i[k] = shfl(a6, gl.base + k); D.a6a[k] = shfl(a6, gl.base + 3 + k);
                     D.a7i[k] = shfl(a7, gl.base + k); D.a7a[k] = shfl(a7, gl.base + 3 + k);
-                    xni[k] = shfl(xn, gl.base + k); xna[k] = shfl(xn, gl.base + 3 + k);
-                    vni[k] = shfl(vn, gl.base + k); vna[k] = shfl(vn, gl.base + 3 + k);
+                    D.xni[k] = shfl(xn, gl.base + k); D.xna[k] = shfl(xn, gl.base + 3 + k);
+                    D.vni[k] = shfl(vn, gl.base + k); D.vna[k] = shfl(vn, gl.base + 3 + k);
                 }
                 D.h = h;
                 D.t = t;
-                if (res == 2 && gl.c == 0) finish_exit(P, D, xni, xna, vni, vna, r2new, fin);
+                if (res == 2 && gl.c == 0) finish_exit(P, D, r2new, fin);
             }
             if (res != 0) {
-                if (gl.c == 0) store_result(P, ic, out, idx, S, fin, true);
+                if (gl.c == 0) store_result(P, ic, out, idx, tally(S), fin, true);
                 active = false;
             }
         }

@@ -340,6 +340,7 @@ struct Final {
 // Everything the exit epilogue needs from an accepted step, in lane-mode layout.
 struct StepData {
     double xi[3], vi[3], xa[3], va[3];  // state at the step start
+    double xni[3], xna[3], vni[3], vna[3];  // state at the step end
     double a1i[3], a1a[3], a3i[3], a3a[3], a4i[3], a4a[3], a5i[3], a5a[3], a6i[3], a6a[3], a7i[3], a7a[3];
     double h, t;
 };
@@ -527,9 +528,7 @@ __device__ __noinline__ double locate_exit(const ExitData& E, double r0sq, doubl
 }
 
 // Final state of a trajectory whose accepted step (data D, end state xn/vn) ends beyond r0 moving out.
-__device__ __noinline__ void finish_exit(const SysDev& P, const StepData& D, const double xni[3],
-                                         const double xna[3], const double vni[3], const double vna[3],
-                                         double r2new, Final& fin)
+__device__ __noinline__ void finish_exit(const SysDev& P, const StepData& D, double r2new, Final& fin)
 {
     const double h = D.h, t = D.t, h2 = h * h;
     double do0 = D.xa[0] - D.xi[0], do1 = D.xa[1] - D.xi[1], do2 = D.xa[2] - D.xi[2];
@@ -577,7 +576,7 @@ __device__ __noinline__ void finish_exit(const SysDev& P, const StepData& D, con
     } else {
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            fin.xi[j] = xni[j]; fin.vi[j] = vni[j]; fin.xa[j] = xna[j]; fin.va[j] = vna[j];
+            fin.xi[j] = D.xni[j]; fin.vi[j] = D.vni[j]; fin.xa[j] = D.xna[j]; fin.va[j] = D.vna[j];
         }
         fin.t = t + h;
         fin.status = ST_EXIT_OUTSIDE;
@@ -694,10 +693,11 @@ __device__ __forceinline__ int lane_attempt(const SysDev& P, Lane& L, Final& fin
                 D.a1i[j] = L.a1i[j]; D.a1a[j] = L.a1a[j]; D.a3i[j] = a3i[j]; D.a3a[j] = a3a[j];
                 D.a4i[j] = a4i[j]; D.a4a[j] = a4a[j]; D.a5i[j] = a5i[j]; D.a5a[j] = a5a[j];
                 D.a6i[j] = a6i[j]; D.a6a[j] = a6a[j]; D.a7i[j] = a7i[j]; D.a7a[j] = a7a[j];
+                D.xni[j] = xni[j]; D.xna[j] = xna[j]; D.vni[j] = vni[j]; D.vna[j] = vna[j];
             }
             D.h = h;
             D.t = t;
-            finish_exit(P, D, xni, xna, vni, vna, r2new, fin);
+            finish_exit(P, D, r2new, fin);
             return FINISHED;
         }
 #pragma unroll
@@ -718,8 +718,26 @@ stop_here:
 }
 
 // Observables of the Fig. 1 caption from the final state; stores one trajectory.
+// Scalars of a finished trajectory needed by the epilogue (passed by value: a reference to the live
+// state would force it into local memory for the whole integration).
+struct Tally {
+    double phi0, t_first, t_last;
+    int n_acc, n_rej, n_bounce;
+};
+__device__ __forceinline__ Tally tally(const Scal& S)
+{
+    Tally T;
+    T.phi0 = S.phi0;
+    T.t_first = S.t_first;
+    T.t_last = S.t_last;
+    T.n_acc = S.n_acc;
+    T.n_rej = S.n_rej;
+    T.n_bounce = S.n_bounce;
+    return T;
+}
+
 __device__ __noinline__ void store_result(const SysDev& P, const IcPtrs& ic, const ObsPtrs& out, long long i,
-                                          const Scal& S, const Final& fin, bool started)
+                                          const Tally S, const Final fin, bool started)
 {
     uint32_t st = fin.status;
     double theta = 0.0, dp = 0.0, dE = 0.0;
