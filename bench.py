@@ -37,17 +37,17 @@ GRID = 1024
 # FP64 floating-point operations per attempted DP5 step of the kernel (fused multiply-add = 2),
 # counted by ncu's per-thread FP64 instruction counters (2 dfma + dmul + dadd, predicated-on threads)
 # on the persistent kernel, divided by the attempted steps of that launch. See profiles/.
-FLOPS_PER_ATTEMPT = 895.0
+FLOPS_PER_ATTEMPT = 902.0
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--stride", type=int, default=4, help="grid stride of the per-step batch")
-    p.add_argument("--warmup-stride", type=int, default=16)
+    p.add_argument("--stride", type=int, default=2, help="grid stride of the per-step batch")
+    p.add_argument("--warmup-stride", type=int, default=64)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--slice-budget", type=int, default=0)
     p.add_argument("--tail-group", type=int, default=0)
     p.add_argument("--tail-blocks-per-sm", type=int, default=0)
+    p.add_argument("--tail-sms", type=int, default=0)
     p.add_argument("--profile-case", action="store_true",
                    help="run the persistent and plain kernels once on a small batch (for ncu) and exit")
     return p.parse_args()
@@ -201,6 +202,15 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def step_inputs(step, stride, rank, world):
+    """Inputs of one step, in queue order (longest expected first)."""
+    from paper_2509_15117_gb300 import schedule as Sch
+    systems, y0, phi0, sid = batch(step, stride, rank, world)
+    speeds = [I.speed_for_energy(I.kelvin(E), s.m_atom) for (sp, E, s) in I.c2_systems()]
+    order = Sch.order_by_cost(sid, Sch.system_cost(systems, speeds))
+    return systems, y0, phi0, sid, order
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -228,28 +238,28 @@ def main():
     stream = torch.cuda.current_stream()
     kw = {"block": args.block, "refill": args.refill, "blocks_per_sm": args.blocks_per_sm,
           "regs_variant": args.regs_variant, "slice_budget": args.slice_budget, "tail_group": args.tail_group,
-          "tail_blocks_per_sm": args.tail_blocks_per_sm}
+          "tail_blocks_per_sm": args.tail_blocks_per_sm, "tail_sms": args.tail_sms}
 
-    # resident inputs for every step (host-side generation outside the timed region)
+    # resident inputs for every step (host-side generation is outside the timed region)
     batches = []
     for s in range(args.steps):
-        systems, y0, phi0, sid = batch(s, args.stride, rank, world)
+        systems, y0, phi0, sid, order = step_inputs(s, args.stride, rank, world)
         y, p, d = Bd.to_device_soa(y0, phi0, sid)
-        batches.append((systems, y, p, d, len(phi0)))
-    descs = [s.as_dict() for s in batches[0][0]]
+        o = torch.from_numpy(order).cuda()
+        batches.append((y, p, d, o, len(phi0)))
+    descs = [s.as_dict() for s in systems]
     sysh = Bd.System(descs)
-    Bd.ia_reserve(sysh.handle, max(b[4] for b in batches), kernel=Bd.IA_KERNEL_PERSISTENT,
-                  **{k: v for k, v in kw.items() if k in ("slice_budget",)})
     n_max = max(b[4] for b in batches)
+    Bd.ia_reserve(sysh.handle, n_max, kernel=Bd.IA_KERNEL_PERSISTENT, slice_budget=args.slice_budget)
     outs = [Bd.alloc_obs(b[4]) for b in batches]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
 
-    # warm-up on smaller batches of the same workload
+    # warm-up steps on small batches of the same workload
     for w in range(args.warmup):
-        systems, y0, phi0, sid = batch(1000 + w, args.warmup_stride, rank, world)
+        systems_w, y0, phi0, sid, order = step_inputs(1000 + w, args.warmup_stride, rank, world)
         y, p, d = Bd.to_device_soa(y0, phi0, sid)
         o = Bd.alloc_obs(len(phi0))
-        Bd.ia_launch(sysh.handle, y, p, d, o, kernel=Bd.IA_KERNEL_PERSISTENT, **kw)
+        Bd.ia_launch(sysh.handle, y, p, d, o, order=torch.from_numpy(order).cuda(), **kw)
     torch.cuda.synchronize()
 
     peak_flops = Bd.ia_fp64_peak(4, 20000)
@@ -259,10 +269,10 @@ def main():
     barrier()
     clocks.start()
     t0 = time.perf_counter()
-    for s, (systems, y, p, d, n) in enumerate(batches):
+    for s, (y, p, d, o, n) in enumerate(batches):
         flush.zero_()
         ev[s][0].record(stream)
-        Bd.ia_launch(sysh.handle, y, p, d, outs[s], kernel=Bd.IA_KERNEL_PERSISTENT, **kw)
+        Bd.ia_launch(sysh.handle, y, p, d, outs[s], order=o, **kw)
         ev[s][1].record(stream)
     barrier()
     wall = time.perf_counter() - t0
@@ -271,6 +281,7 @@ def main():
     total_ms = float(sum(kern_ms))
     n_local = sum(b[4] for b in batches)
     attempts = sum(int((o["n_steps"].to(torch.int64) + o["n_rej"].to(torch.int64)).sum().item()) for o in outs)
+    max_attempts = max(int((o["n_steps"] + o["n_rej"]).max().item()) for o in outs)
     rhs = 6 * attempts + n_local
     tmax_ms = total_ms
     if dist is not None:
@@ -285,29 +296,37 @@ def main():
     value = n_all / (tmax_ms / 1e3)
     achieved = FLOPS_PER_ATTEMPT * attempts / (total_ms / 1e3)
 
-    # plain kernel on the first batch (speedup of the persistent path)
+    # plain kernel against the persistent one on a 1/64 subsample of the first step's batch
     plain = None
     if not args.no_plain:
-        systems, y, p, d, n = batches[0]
-        o = Bd.alloc_obs(n)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        e0.record(stream)
-        Bd.ia_launch(sysh.handle, y, p, d, o, kernel=Bd.IA_KERNEL_PLAIN)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        pms = e0.elapsed_time(e1)
-        plain = {"value": n / (pms / 1e3), "unit": UNIT, "ms": pms,
-                 "persistent_speedup": (n / (kern_ms[0] / 1e3)) / (n / (pms / 1e3))}
+        y, p, d, o, n = batches[0]
+        sub = torch.arange(0, n, 64, device="cuda")
+        ys, ps, ds = y[:, sub].contiguous(), p[sub].contiguous(), d[sub].contiguous()
+        m = int(sub.numel())
+        res = {}
+        for name, kk in (("plain", {"kernel": Bd.IA_KERNEL_PLAIN}), ("persistent", dict(kw))):
+            ob = Bd.alloc_obs(m)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            e0.record(stream)
+            Bd.ia_launch(sysh.handle, ys, ps, ds, ob, **kk)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[name] = e0.elapsed_time(e1)
+        plain = {"value": m / (res["plain"] / 1e3), "unit": UNIT, "trajectories": m, "ms": res["plain"],
+                 "persistent_ms_same_batch": res["persistent"],
+                 "persistent_speedup": res["plain"] / res["persistent"],
+                 "batch": "every 64th trajectory of the step-0 batch, same inputs for both kernels"}
 
     # end to end through the public API: pinned host inputs -> device -> launch -> host outputs
     e2e = None
     if not args.no_e2e:
-        systems, y0, phi0, sid = batch(0, args.stride, rank, world)
+        systems_e, y0, phi0, sid, order = step_inputs(0, args.stride, rank, world)
         n = len(phi0)
         h_y = torch.from_numpy(np.ascontiguousarray(y0.T)).pin_memory()
         h_p = torch.from_numpy(phi0).pin_memory()
         h_s = torch.from_numpy(sid).pin_memory()
+        h_o = torch.from_numpy(order).pin_memory()
         o = Bd.alloc_obs(n)
         host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in o.items()}
         barrier()
@@ -316,13 +335,14 @@ def main():
         y = h_y.to("cuda", non_blocking=True)
         p = h_p.to("cuda", non_blocking=True)
         d = h_s.to("cuda", non_blocking=True)
-        Bd.ia_launch(sysh.handle, y, p, d, o, kernel=Bd.IA_KERNEL_PERSISTENT, **kw)
+        oo = h_o.to("cuda", non_blocking=True)
+        Bd.ia_launch(sysh.handle, y, p, d, o, order=oo, **kw)
         for k in o:
             host_out[k].copy_(o[k], non_blocking=True)
         e1.record(stream)
         barrier()
         ems = e0.elapsed_time(e1)
-        h2d = h_y.numel() * 8 + h_p.numel() * 8 + h_s.numel() * 4
+        h2d = h_y.numel() * 8 + h_p.numel() * 8 + h_s.numel() * 4 + h_o.numel() * 8
         d2h = sum(v.numel() * v.element_size() for v in host_out.values())
         e2e = {"value": n * world / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
@@ -342,12 +362,15 @@ def main():
                             f"D_e = 1 K, q = 0.1, a = 0, Omega = 2 pi 2 MHz, t_max = 1 ms, rtol 1e-10; "
                             f"1024^2 octant grid, every {args.stride}th point per direction per step",
                 "trajectories_per_step": int(n_all / args.steps), "rtol": 1e-10, "kernel": "persistent",
+                "queue_order": "systems by sqrt(m_atom)/speed, descending",
                 "l2": "256 MiB buffer written before each step (inputs < L2)",
                 "block": args.block or 128, "refill": args.refill or 1,
                 "slice_budget": args.slice_budget or 65536, "tail_group": args.tail_group or 6,
+                "tail_sms": args.tail_sms or 8,
             },
             "rhs_evals_per_s": rhs_all / (tmax_ms / 1e3),
             "attempted_steps_per_trajectory": att_all / n_all,
+            "max_attempted_steps": max_attempts,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_flops / 1e12,
                          "unit": "TFLOP/s", "frac": achieved / peak_flops, "traffic": None,
                          "peak_source": "FP64 FMA microbenchmark (ia_fp64_peak) measured in this run",

@@ -85,6 +85,8 @@ typedef struct ia_ic_soa {
     const double* y0;       /* 12 x ld: initial state at t = 0 */
     const double* phi0;     /* n: rf phase at t = 0 */
     const int32_t* sys_id;  /* n: row of the system table, or NULL for row 0 */
+    const int64_t* order;   /* n: persistent launches take trajectories in this order (a permutation of
+                               0..n-1, e.g. longest expected first), or NULL for 0..n-1 */
     int64_t ld;             /* leading dimension of y0 (>= n) */
 } ia_ic_soa;
 
@@ -116,8 +118,9 @@ typedef struct ia_launch_opts {
     int32_t slice_budget;       /* persistent: attempted steps after which a trajectory is handed to the
                                    group-mode tail kernel; 0 = 65536; -1 = never (no tail kernel) */
     int32_t tail_group;         /* lanes per trajectory in the tail kernel: 6 or 8; 0 = 6 */
-    int32_t tail_blocks_per_sm; /* tail kernel blocks (128 threads) per SM, 1..16; 0 = 1 */
-    int32_t reserved;           /* must be 0 */
+    int32_t tail_blocks_per_sm; /* blocks (128 threads) per SM of the clean-up tail kernel, 1..16; 0 = 1 */
+    int32_t tail_sms;           /* persistent: SMs whose single block works on suspended trajectories from
+                                   the start, 1..192; 0 = 8; -1 = none */
     int64_t suspend_capacity;   /* suspend records; 0 = min(n, max(4096, n/32)). A trajectory that finds
                                    no free record is finished by its lane. */
     void* scratch;              /* persistent: caller's device scratch (256-byte aligned), or NULL to use
@@ -157,8 +160,10 @@ int ia_reserve(ia_system* sys, int64_t n, const ia_launch_opts* opts);
  * Fig. 1 observables). Asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
  * n = 0 is a no-op. opts may be NULL (defaults).
  * Persistent launches: a trajectory that has used opts->slice_budget attempted steps is saved to a
- * suspend record and finished by a second kernel that gives each such trajectory a group of lanes,
- * which runs its steps ~3x faster; results are bit-identical to the plain kernel.
+ * suspend record and finished by tail workers that give each such trajectory a group of lanes, which
+ * run its steps ~2.5x faster; tail workers start at once on opts->tail_sms SMs and every other warp
+ * joins them once the queue is drained (one cooperative launch, every wait bounded). Results are
+ * bit-identical to the plain kernel.
  * Concurrency: persistent launches that share the system's own scratch must not overlap; pass a
  * distinct opts->scratch to run them concurrently.
  */
@@ -176,8 +181,8 @@ int ia_launch(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* 
  * IA_STATIC_SCRATCH_BYTES in the library, which every GPU that loads the library keeps until the
  * process exits. It calls no cudaMalloc or cudaFree.
  *   - Limit: ia_scratch_bytes(n, opts) must not exceed IA_STATIC_SCRATCH_BYTES (room for the counters
- *     and 16383 suspend records); otherwise IA_ERR_TOO_LARGE and nothing runs. For large batches set
- *     opts->suspend_capacity <= 16383 (trajectories that find no record finish in their lanes).
+ *     and 16128 suspend records); otherwise IA_ERR_TOO_LARGE and nothing runs. For large batches set
+ *     opts->suspend_capacity <= 16128 (trajectories that find no record finish in their lanes).
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
  *     device current; make that first call before any stream capture. The current device must be the
  *     one the system table was created on (else IA_ERR_INVALID_ARG).

@@ -33,6 +33,7 @@ EXPORTED = ("ia_system_create", "ia_system_destroy", "ia_system_count", "ia_scra
             "ia_launch", "ia_launch_static", "ia_fp64_peak", "ia_rcp_check", "ia_error_string", "ia_version")
 
 IA_STATIC_SCRATCH_BYTES = 4 << 20
+IA_STATIC_MAX_RECORDS = 16128  # suspend records that fit beside the counters and ready flags
 
 
 class IaError(RuntimeError):
@@ -52,7 +53,7 @@ class ia_system_desc(ctypes.Structure):
 
 class ia_ic_soa(ctypes.Structure):
     _fields_ = [("y0", ctypes.c_void_p), ("phi0", ctypes.c_void_p), ("sys_id", ctypes.c_void_p),
-                ("ld", ctypes.c_int64)]
+                ("order", ctypes.c_void_p), ("ld", ctypes.c_int64)]
 
 
 class ia_obs_soa(ctypes.Structure):
@@ -68,7 +69,7 @@ class ia_launch_opts(ctypes.Structure):
                 ("refill", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("regs_variant", ctypes.c_int32), ("slice_budget", ctypes.c_int32),
                 ("tail_group", ctypes.c_int32), ("tail_blocks_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("suspend_capacity", ctypes.c_int64),
+                ("tail_sms", ctypes.c_int32), ("suspend_capacity", ctypes.c_int64),
                 ("scratch", ctypes.c_void_p), ("scratch_bytes", ctypes.c_int64)]
 
 
@@ -210,7 +211,8 @@ def to_device_soa(y0, phi0, sys_id=None, device="cuda"):
 
 def make_opts(kernel: int = IA_KERNEL_PERSISTENT, block: int = 0, grid: int = 0, refill: int = 0,
               blocks_per_sm: int = 0, regs_variant: int = 0, slice_budget: int = 0, tail_group: int = 0,
-              tail_blocks_per_sm: int = 0, suspend_capacity: int = 0, scratch=None) -> ia_launch_opts:
+              tail_blocks_per_sm: int = 0, suspend_capacity: int = 0, scratch=None,
+              tail_sms: int = 0) -> ia_launch_opts:
     opts = ia_launch_opts()
     opts.kernel = kernel
     opts.block = block
@@ -222,6 +224,7 @@ def make_opts(kernel: int = IA_KERNEL_PERSISTENT, block: int = 0, grid: int = 0,
     opts.tail_group = tail_group
     opts.tail_blocks_per_sm = tail_blocks_per_sm
     opts.suspend_capacity = suspend_capacity
+    opts.tail_sms = tail_sms
     if scratch is not None:
         opts.scratch = scratch.data_ptr()
         opts.scratch_bytes = scratch.numel() * scratch.element_size()
@@ -243,31 +246,34 @@ def ia_rcp_check(x, y, stream=None) -> None:
     _check(load().ia_rcp_check(x.data_ptr(), y.data_ptr(), int(x.numel()), _stream_ptr(stream)))
 
 
-def ia_launch(handle: int, y0_soa, phi0, sys_id, out: dict, kernel: int = IA_KERNEL_PERSISTENT,
-              stream=None, **kw) -> None:
-    """Launch on device tensors: y0_soa (12, n) float64, phi0 (n,), sys_id (n,) int32 or None.
-    Keyword options are the fields of ia_launch_opts (see make_opts)."""
+def _ic_struct(y0_soa, phi0, sys_id, order) -> ia_ic_soa:
     n = int(phi0.shape[0])
     ic = ia_ic_soa()
     ic.y0 = y0_soa.data_ptr()
     ic.phi0 = phi0.data_ptr()
     ic.sys_id = sys_id.data_ptr() if sys_id is not None else None
+    ic.order = order.data_ptr() if order is not None else None
     ic.ld = int(y0_soa.stride(0)) if n > 0 else 0
+    return ic
+
+
+def ia_launch(handle: int, y0_soa, phi0, sys_id, out: dict, kernel: int = IA_KERNEL_PERSISTENT,
+              stream=None, order=None, **kw) -> None:
+    """Launch on device tensors: y0_soa (12, n) float64, phi0 (n,), sys_id (n,) int32 or None,
+    order (n,) int64 permutation or None. Keyword options are the fields of ia_launch_opts."""
+    n = int(phi0.shape[0])
+    ic = _ic_struct(y0_soa, phi0, sys_id, order)
     o = _obs_struct(out, n)
     opts = make_opts(kernel=kernel, **kw)
     _check(load().ia_launch(handle, ctypes.byref(ic), n, ctypes.byref(o), ctypes.byref(opts),
                             _stream_ptr(stream)))
 
 
-def ia_launch_static(handle: int, y0_soa, phi0, sys_id, out: dict, stream=None, **kw) -> None:
+def ia_launch_static(handle: int, y0_soa, phi0, sys_id, out: dict, stream=None, order=None, **kw) -> None:
     """Persistent launch whose scratch is the library's fixed device array (allocates nothing).
     Same tensors as ia_launch; keyword options as make_opts (kernel is always persistent)."""
     n = int(phi0.shape[0])
-    ic = ia_ic_soa()
-    ic.y0 = y0_soa.data_ptr()
-    ic.phi0 = phi0.data_ptr()
-    ic.sys_id = sys_id.data_ptr() if sys_id is not None else None
-    ic.ld = int(y0_soa.stride(0)) if n > 0 else 0
+    ic = _ic_struct(y0_soa, phi0, sys_id, order)
     o = _obs_struct(out, n)
     opts = make_opts(kernel=IA_KERNEL_PERSISTENT, **kw)
     _check(load().ia_launch_static(handle, ctypes.byref(ic), n, ctypes.byref(o), ctypes.byref(opts),

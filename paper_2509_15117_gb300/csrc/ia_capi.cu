@@ -2,14 +2,18 @@
 //
 // Kernels:
 //   k_plain       one thread per trajectory; a warp runs until its longest trajectory ends.
-//   k_persistent  a resident grid of lanes; a lane that finishes stores its observables and, once
-//                 `refill` lanes of its warp are idle, the warp claims that many new indices with one
-//                 atomic add on a 64-bit work counter. A trajectory that has used `budget` attempted
-//                 steps is saved to a suspend record and its lane takes new work: trajectory lengths
-//                 span 10^3 .. 10^7 steps (single passes against long-lived complexes).
-//   k_tail<G>     finishes the suspended trajectories, one per group of G lanes (group mode: about a
-//                 third of the FP64 instructions per step of one lane), so the longest complexes,
-//                 which bound the batch time, run ~3x faster per step.
+//   k_sched       the fused persistent kernel (cooperative launch: all blocks resident).
+//                 Lane phase: a lane that finishes stores its observables and, once `refill` lanes of
+//                 its warp are idle, the warp claims that many queue positions with one atomic add.
+//                 A trajectory that has used `budget` attempted steps is saved to a suspend record
+//                 and its lane takes new work: lengths span 10^3 .. 10^7 steps (single passes against
+//                 long-lived complexes).
+//                 Tail phase: suspended trajectories run in group mode (G lanes each, about a third of
+//                 the FP64 instructions per step of one lane, so ~2.5x lower latency). One block on each
+//                 of the first `tail_sms` SMs is a tail worker from the start; every other warp joins
+//                 once the queue is drained. The batch time is then the larger of the bulk work and
+//                 the longest complex's latency, instead of their sum.
+//   k_tail<G>     finishes records the fused kernel left (normally none).
 //   k_fp64_fma    FP64 FMA throughput microbenchmark: the denominator of the integrator's roofline.
 #include <cstdint>
 #include <cstdio>
@@ -26,14 +30,25 @@ using namespace ia;
 
 namespace {
 
-// Work counters at the start of the scratch area.
+// Work counters at the start of the scratch area; suspend-record ready flags and the records follow.
 struct Counters {
-    unsigned long long work;      // next trajectory index for k_persistent
-    unsigned long long n_susp;    // suspend records claimed
-    unsigned long long tail;      // next suspend record for k_tail
-    unsigned long long pad[5];
+    unsigned long long work;        // next queue position for the lane phase
+    unsigned long long n_susp;      // suspend records taken by writers
+    unsigned long long tail;        // next suspend record to resume
+    unsigned long long warps_done;  // warps that have left the lane phase
+    unsigned long long errors;      // bounded waits that ran out (stays 0 in a healthy run)
+    unsigned long long pad[3];
+    unsigned int sm_claim[192];     // blocks seen per SM, to give one block per reserved SM the tail role
 };
-constexpr size_t SCRATCH_HEAD = 256;  // counters, padded so the records start 256-byte aligned
+constexpr size_t SCRATCH_HEAD = 1024;
+static_assert(sizeof(Counters) <= SCRATCH_HEAD, "scratch head");
+constexpr int MAX_TAIL_SMS = 192;
+
+__host__ __device__ constexpr size_t ready_bytes(long long cap) { return ((size_t)cap * 4u + 255u) & ~(size_t)255u; }
+
+// Bounds of the waits in the fused kernel (each wait also sleeps, so these are seconds, not spins).
+constexpr unsigned READY_SPIN_LIMIT = 1u << 22;  // record claimed but not yet published: ~0.3-1 s
+constexpr unsigned IDLE_SPIN_LIMIT = 1u << 27;   // tail worker with nothing to do: minutes
 
 __device__ __forceinline__ void store_bad_sid(const IcPtrs& ic, const ObsPtrs& out, const SysDev* tab, long long i)
 {
@@ -75,12 +90,13 @@ __global__ void __launch_bounds__(128) k_plain(const SysDev* __restrict__ tab, i
     store_result(P, ic, out, i, tally(L.s), fin, true);
 }
 
-// Persistent lane-mode kernel: each lane holds one trajectory at a time.
-template <int BLOCK, int MINB>
-__global__ void __launch_bounds__(BLOCK, MINB) k_persistent(const SysDev* __restrict__ tab, int n_sys, IcPtrs ic,
-                                                            ObsPtrs out, long long n, Counters* __restrict__ ctr,
-                                                            Susp* __restrict__ susp, long long cap, int refill,
-                                                            int budget)
+// Lane phase: each lane holds one trajectory at a time; idle lanes of a warp claim queue positions
+// together with one atomic add; a trajectory that has used `budget` attempted steps is written to a
+// suspend record (published by its ready flag) and the lane takes new work.
+__device__ __forceinline__ void lane_phase(const SysDev* __restrict__ tab, int n_sys, const IcPtrs& ic,
+                                           const ObsPtrs& out, long long n, Counters* __restrict__ ctr,
+                                           unsigned* __restrict__ ready, Susp* __restrict__ susp, long long cap,
+                                           int refill, int budget)
 {
     const int lane = threadIdx.x & 31;
     Lane L;
@@ -99,9 +115,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_persistent(const SysDev* __rest
             if (base + (unsigned long long)n_idle >= (unsigned long long)n) drained = true;
             if (my < 0) {
                 const int rank = __popc(idle & ((1u << lane) - 1u));
-                const unsigned long long cand = base + (unsigned long long)rank;
-                if (cand < (unsigned long long)n) {
-                    my = (long long)cand;
+                const unsigned long long pos = base + (unsigned long long)rank;
+                if (pos < (unsigned long long)n) {
+                    my = ic.order ? __ldg(ic.order + pos) : (long long)pos;
                     sid = ic.sys_id ? __ldg(ic.sys_id + my) : 0;
                     if (sid < 0 || sid >= n_sys) {
                         store_bad_sid(ic, out, tab, my);
@@ -128,6 +144,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_persistent(const SysDev* __rest
                 const unsigned long long slot = atomicAdd(&ctr->n_susp, 1ull);
                 if (slot < (unsigned long long)cap) {
                     lane_suspend(L, my, sid, susp + slot);
+                    __threadfence();
+                    atomicExch(ready + slot, 1u);
                     my = -1;
                 } else {
                     can_suspend = false;  // no room: this lane finishes the trajectory itself
@@ -137,16 +155,36 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_persistent(const SysDev* __rest
     }
 }
 
-// Group-mode kernel for suspended trajectories: one trajectory per group of G lanes.
+// Take the next published-or-being-published suspend record, if any (never beyond the writers).
+__device__ __forceinline__ bool claim_record(Counters* ctr, long long cap, unsigned long long& k)
+{
+    unsigned long long t = *(volatile unsigned long long*)&ctr->tail;
+    for (int it = 0; it < 64; ++it) {
+        const unsigned long long ns = *(volatile unsigned long long*)&ctr->n_susp;
+        const unsigned long long lim = ns < (unsigned long long)cap ? ns : (unsigned long long)cap;
+        if (t >= lim) return false;
+        const unsigned long long prev = atomicCAS(&ctr->tail, t, t + 1);
+        if (prev == t) {
+            k = t;
+            return true;
+        }
+        t = prev;
+    }
+    return false;
+}
+
+// Tail phase (group mode): one suspended trajectory per group of G lanes until it ends.
+// wait_ok: records may still be written by warps in the lane phase (all blocks co-resident,
+// cooperative launch), so an idle group waits for them, boundedly; otherwise an idle group stops
+// as soon as nothing is left to claim.
 template <int G>
-__global__ void __launch_bounds__(128) k_tail(const SysDev* __restrict__ tab, IcPtrs ic, ObsPtrs out,
-                                              const Susp* __restrict__ susp, Counters* __restrict__ ctr,
-                                              long long cap)
+__device__ __forceinline__ void tail_phase(const SysDev* __restrict__ tab, const IcPtrs& ic, const ObsPtrs& out,
+                                           const Susp* __restrict__ susp, const unsigned* __restrict__ ready,
+                                           Counters* __restrict__ ctr, long long cap, bool wait_ok,
+                                           unsigned long long total_warps)
 {
     constexpr int R = (N_COEF + G - 1) / G;  // coefficient rounds per lane
     const GroupLane<G> gl = group_lane<G>();
-    const unsigned long long n_susp_raw = *(volatile unsigned long long*)&ctr->n_susp;
-    const unsigned long long n_susp = n_susp_raw < (unsigned long long)cap ? n_susp_raw : (unsigned long long)cap;
     double x = 0.0, v = 0.0, a1 = 0.0;
     Scal S;
     S.t = 0.0; S.h = 0.0; S.hmin = 0.0; S.phi0 = 0.0; S.rdot_prev = 0.0; S.t_first = 0.0; S.t_last = 0.0;
@@ -154,33 +192,81 @@ __global__ void __launch_bounds__(128) k_tail(const SysDev* __restrict__ tab, Ic
     long long idx = -1;
     int sid = 0;
     bool active = false, drained = false;
+    unsigned idle_spins = 0;
     for (;;) {
         const bool need = !active && !drained;
         if (__any_sync(FULL, need)) {
+            // the group's first lane claims; the claim is broadcast to the group
+            int got = 0;
             unsigned long long k = 0;
-            if (need && gl.c == 0) k = atomicAdd(&ctr->tail, 1ull);
+            if (need && gl.c == 0) {
+                if (claim_record(ctr, cap, k)) {
+                    got = 1;
+                    unsigned spins = 0;
+                    while (*(volatile const unsigned*)(ready + k) == 0u) {
+                        if (++spins > READY_SPIN_LIMIT) {
+                            atomicAdd(&ctr->errors, 1ull);
+                            got = 0;
+                            break;
+                        }
+                        __nanosleep(256);
+                    }
+                    __threadfence();
+                } else {
+                    const bool lane_work_left = wait_ok &&
+                        *(volatile unsigned long long*)&ctr->warps_done < total_warps;
+                    got = lane_work_left ? 2 : 3;  // 2: nothing yet, 3: nothing will come
+                    if (got == 3 && claim_record(ctr, cap, k)) {
+                        // a record published just before the last warp left the lane phase
+                        got = 1;
+                        unsigned spins = 0;
+                        while (*(volatile const unsigned*)(ready + k) == 0u) {
+                            if (++spins > READY_SPIN_LIMIT) {
+                                atomicAdd(&ctr->errors, 1ull);
+                                got = 0;
+                                break;
+                            }
+                            __nanosleep(256);
+                        }
+                        __threadfence();
+                    }
+                }
+            }
+            got = __shfl_sync(FULL, got, gl.base);
             k = __shfl_sync(FULL, k, gl.base);
             if (need) {
-                if (k < n_susp) {
+                if (got == 1) {
+                    // written by another SM during this launch: read through L2
                     const Susp* r = susp + k;
-                    x = r->x[gl.comp];
-                    v = r->v[gl.comp];
-                    a1 = r->a1[gl.comp];
-                    S.t = r->t; S.h = r->h; S.phi0 = r->phi0; S.rdot_prev = r->rdot_prev;
-                    S.t_first = r->t_first; S.t_last = r->t_last;
-                    S.n_acc = r->n_acc; S.n_rej = r->n_rej; S.n_bounce = r->n_bounce;
-                    S.nofailed = (r->flags & 1) != 0;
-                    S.retry = (r->flags & 2) != 0;
+                    x = __ldcg(&r->x[gl.comp]);
+                    v = __ldcg(&r->v[gl.comp]);
+                    a1 = __ldcg(&r->a1[gl.comp]);
+                    S.t = __ldcg(&r->t); S.h = __ldcg(&r->h); S.phi0 = __ldcg(&r->phi0);
+                    S.rdot_prev = __ldcg(&r->rdot_prev);
+                    S.t_first = __ldcg(&r->t_first); S.t_last = __ldcg(&r->t_last);
+                    S.n_acc = __ldcg(&r->n_acc); S.n_rej = __ldcg(&r->n_rej); S.n_bounce = __ldcg(&r->n_bounce);
+                    const int flags = __ldcg(&r->flags);
+                    S.nofailed = (flags & 1) != 0;
+                    S.retry = (flags & 2) != 0;
                     S.hmin = hmin_at(S.t);
-                    idx = r->idx;
-                    sid = r->sid;
+                    idx = __ldcg(&r->idx);
+                    sid = __ldcg(&r->sid);
                     active = true;
-                } else {
+                } else if (got == 3) {
                     drained = true;
                 }
             }
         }
-        if (!__any_sync(FULL, active)) break;
+        if (!__any_sync(FULL, active)) {
+            if (__all_sync(FULL, drained)) break;
+            // nothing to run yet: wait for the lane phase to publish records
+            if (++idle_spins > IDLE_SPIN_LIMIT) {
+                if ((threadIdx.x & 31) == 0) atomicAdd(&ctr->errors, 1ull);
+                break;  // a later launch of the tail kernel finishes what is left
+            }
+            __nanosleep(1000);
+            continue;
+        }
 
         const SysDev& P = tab[sid];
         uint32_t st = 0xffffffffu;
@@ -297,6 +383,49 @@ __global__ void __launch_bounds__(128) k_tail(const SysDev* __restrict__ tab, Ic
     }
 }
 
+// Fused persistent kernel. Blocks on SMs with id < tail_sms (one block per such SM) are tail
+// workers from the start, so long-lived complexes run in group mode on sub-partitions of their own
+// while the rest of the GPU works through the queue; every other block runs the lane phase and then
+// joins the tail phase.
+template <int BLOCK, int MINB, int G>
+__global__ void __launch_bounds__(BLOCK, MINB) k_sched(const SysDev* __restrict__ tab, int n_sys, IcPtrs ic,
+                                                       ObsPtrs out, long long n, Counters* __restrict__ ctr,
+                                                       unsigned* __restrict__ ready, Susp* __restrict__ susp,
+                                                       long long cap, int refill, int budget, int tail_sms,
+                                                       int wait_ok)
+{
+    __shared__ int role;  // 0 lane phase first, 1 tail worker, 2 surplus block on a reserved SM
+    if (threadIdx.x == 0) {
+        int r = 0;
+        if (budget > 0 && tail_sms > 0) {
+            unsigned smid;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            if (smid < (unsigned)tail_sms && smid < (unsigned)MAX_TAIL_SMS)
+                r = (atomicAdd(&ctr->sm_claim[smid], 1u) == 0u) ? 1 : 2;
+        }
+        role = r;
+    }
+    __syncthreads();
+    const int r = role;
+    const unsigned long long total_warps = (unsigned long long)gridDim.x * (BLOCK / 32);
+    if (r == 0) lane_phase(tab, n_sys, ic, out, n, ctr, ready, susp, cap, refill, budget);
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence();
+        atomicAdd(&ctr->warps_done, 1ull);
+    }
+    if (r == 2 || budget <= 0) return;
+    tail_phase<G>(tab, ic, out, susp, ready, ctr, cap, wait_ok != 0, total_warps);
+}
+
+// Finishes suspend records left by k_sched (normally none: its workers drain them).
+template <int G>
+__global__ void __launch_bounds__(128) k_tail(const SysDev* __restrict__ tab, IcPtrs ic, ObsPtrs out,
+                                              const Susp* __restrict__ susp, const unsigned* __restrict__ ready,
+                                              Counters* __restrict__ ctr, long long cap)
+{
+    tail_phase<G>(tab, ic, out, susp, ready, ctr, cap, false, 0ull);
+}
+
 __global__ void k_fp64_fma(double* out, int iters, double a, double b)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -389,6 +518,7 @@ struct Resolved {
 };
 
 constexpr int DEFAULT_BUDGET = 65536;
+constexpr int DEFAULT_TAIL_SMS = 8;
 
 int resolve(int64_t n, const ia_launch_opts* opts, Resolved& r)
 {
@@ -396,7 +526,8 @@ int resolve(int64_t n, const ia_launch_opts* opts, Resolved& r)
     if (opts) r.o = *opts;
     ia_launch_opts& o = r.o;
     if (o.kernel != IA_KERNEL_PLAIN && o.kernel != IA_KERNEL_PERSISTENT) return IA_ERR_INVALID_ARG;
-    if (o.reserved != 0) return IA_ERR_INVALID_ARG;
+    if (o.tail_sms == 0) o.tail_sms = DEFAULT_TAIL_SMS;
+    if (o.tail_sms < -1 || o.tail_sms > MAX_TAIL_SMS) return IA_ERR_INVALID_ARG;
     if (o.refill == 0) o.refill = 1;
     if (o.refill < 1 || o.refill > 32) return IA_ERR_INVALID_ARG;
     if (o.grid < 0 || o.blocks_per_sm < 0 || o.tail_blocks_per_sm < 0) return IA_ERR_INVALID_ARG;
@@ -418,31 +549,19 @@ int resolve(int64_t n, const ia_launch_opts* opts, Resolved& r)
         }
         r.cap = cap;
     }
-    r.bytes = SCRATCH_HEAD + (size_t)r.cap * sizeof(Susp);
+    r.bytes = SCRATCH_HEAD + ready_bytes(r.cap) + (size_t)r.cap * sizeof(Susp);
     return IA_OK;
 }
 
-// Builds of the persistent kernel: (block, minimum resident blocks per SM). The register cap of
-// 3 x 128-thread blocks per SM (168 registers) is the only one that does not spill the step.
-const void* persistent_fn(int block, int minb)
+// Builds of the fused persistent kernel: (block, minimum resident blocks per SM, tail group size).
+// The register cap of 3 x 128-thread blocks per SM (168 registers) is the only one that does not spill.
+const void* sched_fn(int block, int minb, int g)
 {
-    if (block == 64) return (const void*)k_persistent<64, 1>;
-    if (block == 256) return (const void*)k_persistent<256, 1>;
-    if (minb == 3) return (const void*)k_persistent<128, 3>;
-    return (const void*)k_persistent<128, 1>;
-}
-
-void launch_persistent(int block, int minb, int grid, cudaStream_t st, const SysDev* tab, int n_sys, IcPtrs icp,
-                       ObsPtrs op, long long n, Counters* ctr, Susp* susp, long long cap, int refill, int budget)
-{
-    if (block == 64)
-        k_persistent<64, 1><<<grid, 64, 0, st>>>(tab, n_sys, icp, op, n, ctr, susp, cap, refill, budget);
-    else if (block == 256)
-        k_persistent<256, 1><<<grid, 256, 0, st>>>(tab, n_sys, icp, op, n, ctr, susp, cap, refill, budget);
-    else if (minb == 3)
-        k_persistent<128, 3><<<grid, 128, 0, st>>>(tab, n_sys, icp, op, n, ctr, susp, cap, refill, budget);
-    else
-        k_persistent<128, 1><<<grid, 128, 0, st>>>(tab, n_sys, icp, op, n, ctr, susp, cap, refill, budget);
+    if (block == 64) return (const void*)k_sched<64, 1, 6>;
+    if (block == 256) return (const void*)k_sched<256, 1, 6>;
+    if (minb == 3) return (const void*)k_sched<128, 3, 6>;
+    if (g == 8) return (const void*)k_sched<128, 1, 8>;
+    return (const void*)k_sched<128, 1, 6>;
 }
 
 }  // namespace
@@ -560,7 +679,8 @@ int ia_launch(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* 
     const ia_launch_opts& o = r.o;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
-    IcPtrs icp{ic->y0, ic->phi0, ic->sys_id, (long long)ic->ld};
+    IcPtrs icp{ic->y0, ic->phi0, ic->sys_id, reinterpret_cast<const long long*>(ic->order), (long long)ic->ld};
+    if (ic->order && !aligned8(ic->order)) return IA_ERR_ALIGNMENT;
     ObsPtrs op{out->theta_s, out->dp, out->dE_ion, out->t_final, out->t_first_bounce, out->t_last_bounce,
                out->n_bounce, out->status, out->n_steps, out->n_rej, out->y_final,
                (long long)(out->y_final ? out->ld : 0)};
@@ -585,33 +705,55 @@ int ia_launch(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* 
         if (rc != IA_OK) return rc;
         scratch = static_cast<char*>(sys->d_scratch);
     }
-    Counters* ctr = reinterpret_cast<Counters*>(scratch);
-    Susp* susp = reinterpret_cast<Susp*>(scratch + SCRATCH_HEAD);
 
     const int block = o.block == 0 ? 128 : o.block;
     if (block != 64 && block != 128 && block != 256) return IA_ERR_INVALID_ARG;
     if (o.regs_variant != 0 && o.regs_variant != 1 && !(o.regs_variant == 3 && block == 128))
         return IA_ERR_INVALID_ARG;
+    if (o.tail_group == 8 && (block != 128 || o.regs_variant == 3)) return IA_ERR_INVALID_ARG;
     const int minb = o.regs_variant == 3 ? 3 : 1;
-    const void* fn = persistent_fn(block, minb);
+    const void* fn = sched_fn(block, minb, o.tail_group);
+    int resident = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fn, block, 0) != cudaSuccess || resident <= 0)
+        return IA_ERR_CUDA;
     int grid = o.grid;
     if (grid == 0) {
-        int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0) != cudaSuccess || nb <= 0)
-            return IA_ERR_CUDA;
+        int nb = resident;
         if (o.blocks_per_sm > 0 && o.blocks_per_sm < nb) nb = o.blocks_per_sm;
         grid = nb * sys->num_sms;
     }
-    if (cudaMemsetAsync(ctr, 0, sizeof(Counters), st) != cudaSuccess) return IA_ERR_CUDA;
+    // Waiting for records across blocks needs every block resident: a cooperative launch gives that.
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, sys->device);
     const int budget = o.slice_budget > 0 ? o.slice_budget : 0;
-    launch_persistent(block, minb, grid, st, sys->d_tab, sys->n_sys, icp, op, n, ctr, susp, r.cap, o.refill, budget);
-    if (cudaGetLastError() != cudaSuccess) return IA_ERR_CUDA;
+    int wait_ok = (budget > 0 && coop && grid <= resident * sys->num_sms) ? 1 : 0;
+    int tail_sms = (wait_ok && o.tail_sms > 0) ? o.tail_sms : 0;
+    if (tail_sms > sys->num_sms / 2) tail_sms = sys->num_sms / 2;
+
+    Counters* ctr = reinterpret_cast<Counters*>(scratch);
+    unsigned* ready = reinterpret_cast<unsigned*>(scratch + SCRATCH_HEAD);
+    Susp* susp = reinterpret_cast<Susp*>(scratch + SCRATCH_HEAD + ready_bytes(r.cap));
+    if (cudaMemsetAsync(scratch, 0, SCRATCH_HEAD + ready_bytes(r.cap), st) != cudaSuccess) return IA_ERR_CUDA;
+    long long cap = r.cap;
+    long long nn = (long long)n;
+    int refill = o.refill;
+    int n_sys = sys->n_sys;
+    const SysDev* tab = sys->d_tab;
+    void* args[] = {(void*)&tab, (void*)&n_sys, (void*)&icp, (void*)&op, (void*)&nn, (void*)&ctr, (void*)&ready,
+                    (void*)&susp, (void*)&cap, (void*)&refill, (void*)&budget, (void*)&tail_sms, (void*)&wait_ok};
+    cudaError_t e;
+    if (wait_ok)
+        e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, st);
+    else
+        e = cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, st);
+    if (e != cudaSuccess) return IA_ERR_CUDA;
     if (budget > 0) {
+        // records the fused kernel could not finish (normally none)
         const int tgrid = o.tail_blocks_per_sm * sys->num_sms;
         if (o.tail_group == 8)
-            k_tail<8><<<tgrid, 128, 0, st>>>(sys->d_tab, icp, op, susp, ctr, r.cap);
+            k_tail<8><<<tgrid, 128, 0, st>>>(tab, icp, op, susp, ready, ctr, cap);
         else
-            k_tail<6><<<tgrid, 128, 0, st>>>(sys->d_tab, icp, op, susp, ctr, r.cap);
+            k_tail<6><<<tgrid, 128, 0, st>>>(tab, icp, op, susp, ready, ctr, cap);
         if (cudaGetLastError() != cudaSuccess) return IA_ERR_CUDA;
     }
     return IA_OK;

@@ -76,6 +76,7 @@ struct IcPtrs {
     const double* y0;
     const double* phi0;
     const int32_t* sys_id;
+    const long long* order;  // queue position -> trajectory index, or null (identity)
     long long ld;
 };
 

@@ -49,7 +49,7 @@ def test_error_strings_and_version_without_gpu():
 def test_struct_layouts_match_header():
     # sizes of the C structs as the header defines them (x86-64 / aarch64 LP64)
     assert ctypes.sizeof(Bd.ia_system_desc) == 8 * 17 + 4 * 2 + 8
-    assert ctypes.sizeof(Bd.ia_ic_soa) == 8 * 4
+    assert ctypes.sizeof(Bd.ia_ic_soa) == 8 * 5
     assert ctypes.sizeof(Bd.ia_obs_soa) == 8 * 12
     assert ctypes.sizeof(Bd.ia_launch_opts) == 4 * 10 + 8 * 3
 
@@ -62,9 +62,11 @@ def test_invalid_arguments_rejected_without_touching_gpu():
     assert L.ia_system_count(None) == -1
     assert L.ia_system_destroy(None) == 0
     # scratch sizing is pure host arithmetic
-    assert Bd.ia_scratch_bytes(0) == 256
-    assert Bd.ia_scratch_bytes(100000, kernel=Bd.IA_KERNEL_PERSISTENT) == 256 + 256 * 4096
-    assert Bd.ia_scratch_bytes(1 << 20, kernel=Bd.IA_KERNEL_PERSISTENT) == 256 + 256 * (1 << 15)
-    assert Bd.ia_scratch_bytes(1000, kernel=Bd.IA_KERNEL_PERSISTENT, slice_budget=-1) == 256
+    head = 1024
+    assert Bd.ia_scratch_bytes(0) == head
+    assert Bd.ia_scratch_bytes(100000, kernel=Bd.IA_KERNEL_PERSISTENT) == head + 4 * 4096 + 256 * 4096
+    assert Bd.ia_scratch_bytes(1 << 20, kernel=Bd.IA_KERNEL_PERSISTENT) == head + 4 * (1 << 15) + 256 * (1 << 15)
+    assert Bd.ia_scratch_bytes(1000, kernel=Bd.IA_KERNEL_PERSISTENT, slice_budget=-1) == head
+    assert Bd.ia_scratch_bytes(1000, kernel=Bd.IA_KERNEL_PERSISTENT, suspend_capacity=5) == head + 256 + 5 * 256
     with pytest.raises(Bd.IaError):
         Bd.ia_scratch_bytes(10, kernel=Bd.IA_KERNEL_PERSISTENT, tail_group=5)

@@ -87,7 +87,7 @@ def test_suspend_overflow_and_caller_scratch(c1, torch_cuda):
     a = run_gpu(descs, y0[:n], phi0[:n], sid[:n], Bd.IA_KERNEL_PLAIN)
     kw = dict(kernel=Bd.IA_KERNEL_PERSISTENT, slice_budget=200, suspend_capacity=5)
     nbytes = Bd.ia_scratch_bytes(n, **kw)
-    assert nbytes == 256 + 5 * 256
+    assert nbytes == 1024 + 256 + 5 * 256
     scratch = torch.zeros(nbytes // 8, dtype=torch.float64, device="cuda")
     assert scratch.data_ptr() % 256 == 0
     with Bd.System(descs) as S:
@@ -96,10 +96,32 @@ def test_suspend_overflow_and_caller_scratch(c1, torch_cuda):
         Bd.ia_launch(S.handle, yd, pd, sd, out, scratch=scratch, **{k: v for k, v in kw.items() if k != "kernel"})
         torch.cuda.synchronize()
         b = Bd.to_numpy(out)
-        ctr = scratch[:3].view(torch.int64).cpu().numpy()
+        ctr = scratch[:5].view(torch.int64).cpu().numpy()
     assert ctr[1] > 5  # more trajectories asked to suspend than there was room for
+    assert ctr[4] == 0  # no bounded wait ran out
     for k in a:
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+def test_queue_order_and_noncooperative_fallback(c1, torch_cuda):
+    """A work-queue permutation, and a grid too large for a cooperative launch (tail workers then never
+    wait), change only the schedule: same bits as the plain kernel."""
+    torch = torch_cuda
+    descs, y0, phi0, sid, orc, spread = c1
+    n = 600
+    a = run_gpu(descs, y0[:n], phi0[:n], sid[:n], Bd.IA_KERNEL_PLAIN)
+    perm = torch.from_numpy(np.random.default_rng(3).permutation(n).astype(np.int64)).cuda()
+    with Bd.System(descs) as S:
+        yd, pd, sd = Bd.to_device_soa(y0[:n], phi0[:n], sid[:n])
+        for kw in ({"order": perm, "slice_budget": 400, "tail_sms": 4},
+                   {"order": perm, "slice_budget": 400, "grid": 2000},
+                   {"slice_budget": 400, "tail_sms": -1}):
+            out = Bd.alloc_obs(n)
+            Bd.ia_launch(S.handle, yd, pd, sd, out, **kw)
+            torch.cuda.synchronize()
+            b = Bd.to_numpy(out)
+            for k in a:
+                np.testing.assert_array_equal(a[k], b[k], err_msg=f"{k} {list(kw)}")
 
 
 def test_rcp_newton_accuracy(torch_cuda):

@@ -55,12 +55,13 @@ def test_static_launch_rejects_sizes_beyond_its_array(cuda):
     with Bd.System(descs) as S:
         yd, pd, sd = Bd.to_device_soa(y0, phi0, sid)
         out = Bd.alloc_obs(len(phi0))
-        too_many = Bd.IA_STATIC_SCRATCH_BYTES // 256  # records needed exceed the array
+        fits = Bd.IA_STATIC_MAX_RECORDS
         assert Bd.ia_scratch_bytes(len(phi0), kernel=Bd.IA_KERNEL_PERSISTENT,
-                                   suspend_capacity=too_many) > Bd.IA_STATIC_SCRATCH_BYTES
+                                   suspend_capacity=fits) <= Bd.IA_STATIC_SCRATCH_BYTES
+        assert Bd.ia_scratch_bytes(len(phi0), kernel=Bd.IA_KERNEL_PERSISTENT,
+                                   suspend_capacity=fits + 1) > Bd.IA_STATIC_SCRATCH_BYTES
         with pytest.raises(Bd.IaError, match="size beyond"):
-            Bd.ia_launch_static(S.handle, yd, pd, sd, out, suspend_capacity=too_many)
+            Bd.ia_launch_static(S.handle, yd, pd, sd, out, suspend_capacity=fits + 1)
         # the largest capacity that fits is accepted
-        fits = (Bd.IA_STATIC_SCRATCH_BYTES - 256) // 256
         Bd.ia_launch_static(S.handle, yd, pd, sd, out, suspend_capacity=fits)
         cuda.cuda.synchronize()
