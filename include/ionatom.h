@@ -202,6 +202,70 @@ int ia_launch_static(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_ob
  */
 int ia_fp64_peak(int32_t blocks_per_sm, int32_t iters, void* stream, double* flops);
 
+/* ---- batch statistics ---- */
+#define IA_STATS_BOUNCE_BINS 32
+#define IA_STATS_LIFETIME_BINS 64
+#define IA_STATS_EXIT_SLOT 6
+#define IA_STATS_MAX_CELLS 1024
+
+/* Per-cell ensemble statistics: the quantities of the paper's Fig. 3 and Fig. 4 (probability of
+ * complex formation), Fig. 1c (bounce counts) and Fig. 2 (complex lifetimes), plus ion heating. */
+typedef struct ia_stats {
+    int64_t n;                 /* trajectories in the cell */
+    int64_t n_complex;         /* trajectories with n_bounce >= 2 */
+    int64_t attempts;          /* attempted steps (accepted + rejected) */
+    int64_t n_status[8];       /* [b], b = 0..5: trajectories with status bit b (IA_ST_TMAX .. IA_ST_EXIT_OUTSIDE);
+                                  [IA_STATS_EXIT_SLOT]: clean exits (low status byte 0); [7]: 0 */
+    int64_t bounce_hist[IA_STATS_BOUNCE_BINS];     /* [0]: no bounce; [k >= 1]: 2^(k-1) <= n_bounce < 2^k
+                                                      (last bin open-ended) */
+    int64_t lifetime_hist[IA_STATS_LIFETIME_BINS]; /* complexes by tau = t_last_bounce - t_first_bounce:
+                                                      bin k = floor(2 (log2 tau - 20)), clamped to 0..63 */
+    double sum_dE;             /* sum of dE_ion, added in a fixed order (bit-reproducible) */
+    double sum_dE2;            /* sum of dE_ion^2, same order */
+} ia_stats;
+
+/*
+ * Reduce the observables of n trajectories into n_cells ia_stats records (device array `stats`,
+ * caller-owned, overwritten). cell_id: device array of n cell indices in 0..n_cells-1 (others are
+ * skipped), or NULL to put every trajectory in cell 0. n_cells: 1..IA_STATS_MAX_CELLS. Uses the
+ * system's scratch (grown synchronously when too small; call ia_reserve_stats before a capture).
+ * Asynchronous on `stream`.
+ */
+int ia_reduce_stats(ia_system* sys, const ia_obs_soa* obs, int64_t n, const int32_t* cell_id, int32_t n_cells,
+                    ia_stats* stats, void* stream);
+
+/* Grow the system's statistics scratch for n trajectories and n_cells cells (synchronous). */
+int ia_reserve_stats(ia_system* sys, int64_t n, int32_t n_cells);
+
+/* ---- CUDA graph of one batch ---- */
+typedef struct ia_graph ia_graph; /* opaque */
+
+/*
+ * Capture one persistent launch (ia_launch with opts, kernel forced to IA_KERNEL_PERSISTENT) followed,
+ * if stats is not NULL, by ia_reduce_stats into a CUDA graph on `stream` (a stream created by the
+ * caller; the legacy default stream cannot be captured), and instantiate it. Scratch is reserved
+ * first. All pointers are baked into the graph: replays read the same input buffers and write the same
+ * outputs, so the caller refills the inputs between replays. Nothing runs until ia_graph_launch.
+ */
+int ia_graph_create(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* out,
+                    const ia_launch_opts* opts, const int32_t* cell_id, int32_t n_cells, ia_stats* stats,
+                    void* stream, ia_graph** graph);
+/* Replay the captured batch on `stream`. */
+int ia_graph_launch(ia_graph* graph, void* stream);
+/* Free a graph (NULL accepted); no replay may be in flight. */
+int ia_graph_destroy(ia_graph* graph);
+
+/*
+ * Autotuner of the persistent kernel's lane phase (block size, register cap, refill grain). Each
+ * candidate integrates the n trajectories of `ic` (a sample of the batch to tune for) with every
+ * trajectory stopped after `attempt_cap` attempted steps (no tail phase, outputs not written), timed
+ * with CUDA events on `stream`; every candidate does the same arithmetic, so the fastest has the
+ * highest lane-phase throughput. Writes the winner into *best (other fields copied from *base, which
+ * may be NULL) and its time in *best_ms. Synchronous. attempt_cap: 64..1048576.
+ */
+int ia_autotune(ia_system* sys, const ia_ic_soa* ic, int64_t n, int32_t attempt_cap, const ia_launch_opts* base,
+                ia_launch_opts* best, double* best_ms, void* stream);
+
 /*
  * Test hook (no counterpart in the paper): y[i] = 1/x[i] computed as the integrator computes 1/r^2
  * (Newton-Raphson from an FP32 seed). x, y: device arrays of n doubles, x[i] > 0. Asynchronous.

@@ -30,7 +30,18 @@ ST_EXIT_OUTSIDE = 1 << 5
 ST_COMPLEX = 1 << 8
 
 EXPORTED = ("ia_system_create", "ia_system_destroy", "ia_system_count", "ia_scratch_bytes", "ia_reserve",
-            "ia_launch", "ia_launch_static", "ia_fp64_peak", "ia_rcp_check", "ia_error_string", "ia_version")
+            "ia_launch", "ia_launch_static", "ia_reduce_stats", "ia_reserve_stats", "ia_graph_create",
+            "ia_graph_launch", "ia_graph_destroy", "ia_autotune", "ia_fp64_peak", "ia_rcp_check",
+            "ia_error_string", "ia_version")
+
+STATS_BOUNCE_BINS = 32
+STATS_LIFETIME_BINS = 64
+STATS_EXIT_SLOT = 6
+STATS_DTYPE = np.dtype([
+    ("n", "<i8"), ("n_complex", "<i8"), ("attempts", "<i8"), ("n_status", "<i8", (8,)),
+    ("bounce_hist", "<i8", (STATS_BOUNCE_BINS,)), ("lifetime_hist", "<i8", (STATS_LIFETIME_BINS,)),
+    ("sum_dE", "<f8"), ("sum_dE2", "<f8"),
+])
 
 IA_STATIC_SCRATCH_BYTES = 4 << 20
 IA_STATIC_MAX_RECORDS = 16128  # suspend records that fit beside the counters and ready flags
@@ -101,6 +112,22 @@ def load(build_if_missing: bool = True):
     L.ia_launch_static.argtypes = [ctypes.c_void_p, P(ia_ic_soa), ctypes.c_int64, P(ia_obs_soa),
                                    P(ia_launch_opts), ctypes.c_void_p]
     L.ia_launch_static.restype = ctypes.c_int
+    L.ia_reduce_stats.argtypes = [ctypes.c_void_p, P(ia_obs_soa), ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32,
+                                  ctypes.c_void_p, ctypes.c_void_p]
+    L.ia_reduce_stats.restype = ctypes.c_int
+    L.ia_reserve_stats.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]
+    L.ia_reserve_stats.restype = ctypes.c_int
+    L.ia_graph_create.argtypes = [ctypes.c_void_p, P(ia_ic_soa), ctypes.c_int64, P(ia_obs_soa), P(ia_launch_opts),
+                                  ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                  P(ctypes.c_void_p)]
+    L.ia_graph_create.restype = ctypes.c_int
+    L.ia_graph_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.ia_graph_launch.restype = ctypes.c_int
+    L.ia_graph_destroy.argtypes = [ctypes.c_void_p]
+    L.ia_graph_destroy.restype = ctypes.c_int
+    L.ia_autotune.argtypes = [ctypes.c_void_p, P(ia_ic_soa), ctypes.c_int64, ctypes.c_int32, P(ia_launch_opts),
+                              P(ia_launch_opts), P(ctypes.c_double), ctypes.c_void_p]
+    L.ia_autotune.restype = ctypes.c_int
     L.ia_scratch_bytes.argtypes = [ctypes.c_int64, P(ia_launch_opts)]
     L.ia_scratch_bytes.restype = ctypes.c_int64
     L.ia_reserve.argtypes = [ctypes.c_void_p, ctypes.c_int64, P(ia_launch_opts)]
@@ -278,6 +305,71 @@ def ia_launch_static(handle: int, y0_soa, phi0, sys_id, out: dict, stream=None, 
     opts = make_opts(kernel=IA_KERNEL_PERSISTENT, **kw)
     _check(load().ia_launch_static(handle, ctypes.byref(ic), n, ctypes.byref(o), ctypes.byref(opts),
                                    _stream_ptr(stream)))
+
+
+def alloc_stats(n_cells: int, device="cuda"):
+    """Device buffer for n_cells ia_stats records (raw bytes)."""
+    import torch
+    return torch.empty(n_cells * STATS_DTYPE.itemsize, dtype=torch.uint8, device=device)
+
+
+def ia_reduce_stats(handle: int, out: dict, n: int, cell_id, n_cells: int, stats, stream=None) -> None:
+    """Reduce device observables into the device stats buffer (see alloc_stats)."""
+    o = _obs_struct(out, n)
+    _check(load().ia_reduce_stats(handle, ctypes.byref(o), n, cell_id.data_ptr() if cell_id is not None else None,
+                                  n_cells, stats.data_ptr(), _stream_ptr(stream)))
+
+
+def ia_reserve_stats(handle: int, n: int, n_cells: int) -> None:
+    _check(load().ia_reserve_stats(handle, n, n_cells))
+
+
+def stats_to_numpy(stats) -> np.ndarray:
+    return np.frombuffer(stats.cpu().numpy().tobytes(), dtype=STATS_DTYPE).copy()
+
+
+class Graph:
+    """A captured batch (persistent launch + optional statistics) replayed with ia_graph_launch."""
+
+    def __init__(self, handle: int, y0_soa, phi0, sys_id, out: dict, stream, order=None, cell_id=None,
+                 n_cells: int = 0, stats=None, **kw):
+        n = int(phi0.shape[0])
+        self._keep = (y0_soa, phi0, sys_id, out, order, cell_id, stats)
+        ic = _ic_struct(y0_soa, phi0, sys_id, order)
+        o = _obs_struct(out, n)
+        opts = make_opts(kernel=IA_KERNEL_PERSISTENT, **kw)
+        g = ctypes.c_void_p()
+        _check(load().ia_graph_create(handle, ctypes.byref(ic), n, ctypes.byref(o), ctypes.byref(opts),
+                                      cell_id.data_ptr() if cell_id is not None else None, n_cells,
+                                      stats.data_ptr() if stats is not None else None,
+                                      ctypes.c_void_p(stream.cuda_stream), ctypes.byref(g)))
+        self.ptr = g.value
+
+    def launch(self, stream) -> None:
+        _check(load().ia_graph_launch(self.ptr, ctypes.c_void_p(stream.cuda_stream)))
+
+    def close(self) -> None:
+        if self.ptr:
+            _check(load().ia_graph_destroy(self.ptr))
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ia_autotune(handle: int, y0_soa, phi0, sys_id, attempt_cap: int = 1024, order=None, stream=None, **base):
+    """Lane-phase autotuner on a sample (device tensors); returns (options dict, best ms)."""
+    n = int(phi0.shape[0])
+    ic = _ic_struct(y0_soa, phi0, sys_id, order)
+    b = make_opts(kernel=IA_KERNEL_PERSISTENT, **base)
+    best = ia_launch_opts()
+    ms = ctypes.c_double()
+    _check(load().ia_autotune(handle, ctypes.byref(ic), n, attempt_cap, ctypes.byref(b), ctypes.byref(best),
+                              ctypes.byref(ms), _stream_ptr(stream)))
+    return {"block": best.block, "regs_variant": best.regs_variant, "refill": best.refill}, ms.value
 
 
 class System:

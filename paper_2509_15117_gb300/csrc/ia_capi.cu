@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "ia_traj.cuh"
+#include "ia_stats.cuh"
 #include "../../include/ionatom.h"
 
 using namespace ia;
@@ -453,9 +454,16 @@ struct ia_system {
     int device;
     int n_sys;
     SysDev* d_tab;
-    void* d_scratch;          // library-owned scratch (grown on demand)
+    void* d_scratch;          // library-owned scratch of persistent launches (grown on demand)
     size_t scratch_bytes;
+    void* d_stats_scratch;    // block partials of the statistics reduction
+    size_t stats_scratch_bytes;
     int num_sms;
+};
+
+struct ia_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
 };
 
 namespace {
@@ -607,6 +615,8 @@ int ia_system_create(const ia_system_desc* desc, int32_t n_sys, ia_system** out)
     s->d_tab = nullptr;
     s->d_scratch = nullptr;
     s->scratch_bytes = 0;
+    s->d_stats_scratch = nullptr;
+    s->stats_scratch_bytes = 0;
     s->num_sms = prop.multiProcessorCount;
     if (cudaMalloc(&s->d_tab, sizeof(SysDev) * (size_t)n_sys) != cudaSuccess ||
         cudaMemcpy(s->d_tab, host, sizeof(SysDev) * (size_t)n_sys, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -625,6 +635,7 @@ int ia_system_destroy(ia_system* sys)
     if (!sys) return IA_OK;
     cudaFree(sys->d_tab);
     cudaFree(sys->d_scratch);
+    cudaFree(sys->d_stats_scratch);
     delete sys;
     return IA_OK;
 }
@@ -756,6 +767,212 @@ int ia_launch(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* 
             k_tail<6><<<tgrid, 128, 0, st>>>(tab, icp, op, susp, ready, ctr, cap);
         if (cudaGetLastError() != cudaSuccess) return IA_ERR_CUDA;
     }
+    return IA_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batch statistics
+
+namespace {
+int stats_grid(const ia_system* sys, int64_t n)
+{
+    long long g = (n + STATS_BLOCK - 1) / STATS_BLOCK;
+    const long long gmax = 4LL * sys->num_sms;
+    if (g > gmax) g = gmax;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+}  // namespace
+
+int ia_reserve_stats(ia_system* sys, int64_t n, int32_t n_cells)
+{
+    if (!sys || n < 0 || n_cells < 1 || n_cells > IA_STATS_MAX_CELLS) return IA_ERR_INVALID_ARG;
+    const size_t need = (size_t)stats_grid(sys, n) * (size_t)n_cells * 2 * sizeof(double);
+    if (need <= sys->stats_scratch_bytes) return IA_OK;
+    void* p = nullptr;
+    if (cudaMalloc(&p, need) != cudaSuccess) return IA_ERR_CUDA;
+    cudaFree(sys->d_stats_scratch);
+    sys->d_stats_scratch = p;
+    sys->stats_scratch_bytes = need;
+    return IA_OK;
+}
+
+int ia_reduce_stats(ia_system* sys, const ia_obs_soa* obs, int64_t n, const int32_t* cell_id, int32_t n_cells,
+                    ia_stats* stats, void* stream)
+{
+    if (!sys || !obs || !stats || n < 0 || n_cells < 1 || n_cells > IA_STATS_MAX_CELLS) return IA_ERR_INVALID_ARG;
+    if (n > 0 && (!obs->status || !obs->n_bounce || !obs->n_steps || !obs->n_rej || !obs->dE_ion ||
+                  !obs->t_first_bounce || !obs->t_last_bounce))
+        return IA_ERR_INVALID_ARG;
+    if (!aligned8(stats) || (n > 0 && !aligned8(obs->dE_ion))) return IA_ERR_ALIGNMENT;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(stats, 0, sizeof(ia_stats) * (size_t)n_cells, st) != cudaSuccess) return IA_ERR_CUDA;
+    const int grid = stats_grid(sys, n);
+    int rc = ia_reserve_stats(sys, n, n_cells);
+    if (rc != IA_OK) return rc;
+    double* partial = static_cast<double*>(sys->d_stats_scratch);
+    long long chunk = (n + grid - 1) / grid;
+    chunk = (chunk + 31) / 32 * 32;
+    const size_t shmem = (size_t)(STATS_BLOCK / 32) * n_cells * 2 * sizeof(double);
+    if (shmem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_stats_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem) != cudaSuccess)
+        return IA_ERR_CUDA;
+    ObsPtrs op{obs->theta_s, obs->dp, obs->dE_ion, obs->t_final, obs->t_first_bounce, obs->t_last_bounce,
+               obs->n_bounce, obs->status, obs->n_steps, obs->n_rej, nullptr, 0};
+    k_stats_pass1<<<grid, STATS_BLOCK, shmem, st>>>(op, (long long)n, cell_id, n_cells, stats, partial, chunk);
+    k_stats_pass2<<<(n_cells + 127) / 128, 128, 0, st>>>(partial, grid, n_cells, stats);
+    return cudaGetLastError() == cudaSuccess ? IA_OK : IA_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------------------------
+// CUDA graph of one batch
+
+int ia_graph_create(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* out,
+                    const ia_launch_opts* opts, const int32_t* cell_id, int32_t n_cells, ia_stats* stats,
+                    void* stream, ia_graph** graph)
+{
+    if (!sys || !ic || !out || !graph || !stream || n < 1) return IA_ERR_INVALID_ARG;
+    ia_launch_opts o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    o.kernel = IA_KERNEL_PERSISTENT;
+    int rc = IA_OK;
+    if (!o.scratch) rc = ia_reserve(sys, n, &o);
+    if (rc == IA_OK && stats) rc = ia_reserve_stats(sys, n, n_cells);
+    if (rc != IA_OK) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return IA_ERR_CUDA;
+    rc = ia_launch(sys, ic, n, out, &o, stream);
+    if (rc == IA_OK && stats) rc = ia_reduce_stats(sys, out, n, cell_id, n_cells, stats, stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &g);
+    if (rc != IA_OK || ec != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        return rc != IA_OK ? rc : IA_ERR_CUDA;
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return IA_ERR_CUDA;
+    }
+    ia_graph* G = new (std::nothrow) ia_graph;
+    if (!G) {
+        cudaGraphExecDestroy(ex);
+        cudaGraphDestroy(g);
+        return IA_ERR_INVALID_ARG;
+    }
+    G->graph = g;
+    G->exec = ex;
+    *graph = G;
+    return IA_OK;
+}
+
+int ia_graph_launch(ia_graph* graph, void* stream)
+{
+    if (!graph) return IA_ERR_INVALID_ARG;
+    return cudaGraphLaunch(graph->exec, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? IA_OK : IA_ERR_CUDA;
+}
+
+int ia_graph_destroy(ia_graph* graph)
+{
+    if (!graph) return IA_OK;
+    cudaGraphExecDestroy(graph->exec);
+    cudaGraphDestroy(graph->graph);
+    delete graph;
+    return IA_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Autotuner of the lane phase
+
+int ia_autotune(ia_system* sys, const ia_ic_soa* ic, int64_t n, int32_t attempt_cap, const ia_launch_opts* base,
+                ia_launch_opts* best, double* best_ms, void* stream)
+{
+    if (!sys || !ic || !best || !best_ms || n < 1 || attempt_cap < 64 || attempt_cap > (1 << 20))
+        return IA_ERR_INVALID_ARG;
+    if (!ic->y0 || !ic->phi0 || ic->ld < n) return IA_ERR_INVALID_ARG;
+    ia_launch_opts b0;
+    std::memset(&b0, 0, sizeof(b0));
+    if (base) b0 = *base;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // throw-away outputs and a suspend area with room for every trajectory (each stops at the cap)
+    const size_t nn = (size_t)n;
+    const size_t obs_bytes = nn * (6 * sizeof(double) + 4 * sizeof(int32_t));
+    const long long cap = (long long)n;
+    const size_t scr_bytes = SCRATCH_HEAD + ready_bytes(cap) + (size_t)cap * sizeof(Susp);
+    char* obuf = nullptr;
+    char* scr = nullptr;
+    if (cudaMalloc(&obuf, obs_bytes) != cudaSuccess) return IA_ERR_CUDA;
+    if (cudaMalloc(&scr, scr_bytes) != cudaSuccess) {
+        cudaFree(obuf);
+        return IA_ERR_CUDA;
+    }
+    ObsPtrs op;
+    op.theta_s = (double*)obuf;
+    op.dp = op.theta_s + nn;
+    op.dE_ion = op.dp + nn;
+    op.t_final = op.dE_ion + nn;
+    op.t_first = op.t_final + nn;
+    op.t_last = op.t_first + nn;
+    op.n_bounce = (int32_t*)(op.t_last + nn);
+    op.status = (uint32_t*)(op.n_bounce + nn);
+    op.n_steps = (int32_t*)(op.status + nn);
+    op.n_rej = op.n_steps + nn;
+    op.y_final = nullptr;
+    op.ld_out = 0;
+    IcPtrs icp{ic->y0, ic->phi0, ic->sys_id, reinterpret_cast<const long long*>(ic->order), (long long)ic->ld};
+    Counters* ctr = reinterpret_cast<Counters*>(scr);
+    unsigned* ready = reinterpret_cast<unsigned*>(scr + SCRATCH_HEAD);
+    Susp* susp = reinterpret_cast<Susp*>(scr + SCRATCH_HEAD + ready_bytes(cap));
+    struct Cand { int block, minb, refill; };
+    const Cand cands[] = {{128, 1, 1}, {128, 1, 4}, {128, 1, 16}, {64, 1, 1}, {64, 1, 4},
+                          {256, 1, 1}, {256, 1, 4}, {128, 3, 1}, {128, 3, 4}};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = IA_OK;
+    double best_t = 1e300;
+    Cand win = cands[0];
+    for (int c = -1; c < (int)(sizeof(cands) / sizeof(cands[0])) && rc == IA_OK; ++c) {
+        const Cand cd = cands[c < 0 ? 0 : c];  // c = -1: warm-up of the first candidate
+        const void* fn = sched_fn(cd.block, cd.minb, 6);
+        int resident = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fn, cd.block, 0) != cudaSuccess || resident <= 0) {
+            rc = IA_ERR_CUDA;
+            break;
+        }
+        int grid = resident * sys->num_sms;
+        long long nn_ = (long long)n;
+        int refill = cd.refill, budget = attempt_cap, tail_sms = 0, wait_ok = 0, n_sys = sys->n_sys;
+        long long capv = cap;
+        const SysDev* tab = sys->d_tab;
+        void* args[] = {(void*)&tab, (void*)&n_sys, (void*)&icp, (void*)&op, (void*)&nn_, (void*)&ctr,
+                        (void*)&ready, (void*)&susp, (void*)&capv, (void*)&refill, (void*)&budget,
+                        (void*)&tail_sms, (void*)&wait_ok};
+        if (cudaMemsetAsync(scr, 0, SCRATCH_HEAD + ready_bytes(cap), st) != cudaSuccess) rc = IA_ERR_CUDA;
+        cudaEventRecord(e0, st);
+        // budget > 0 with no tail workers: the kernel stops every trajectory at the cap
+        if (rc == IA_OK && cudaLaunchKernel(fn, dim3(grid), dim3(cd.block), args, 0, st) != cudaSuccess) rc = IA_ERR_CUDA;
+        cudaEventRecord(e1, st);
+        if (rc == IA_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = IA_ERR_CUDA;
+        float ms = 0.0f;
+        if (rc == IA_OK) cudaEventElapsedTime(&ms, e0, e1);
+        if (c >= 0 && rc == IA_OK && ms < best_t) {
+            best_t = ms;
+            win = cd;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(obuf);
+    cudaFree(scr);
+    if (rc != IA_OK) return rc;
+    *best = b0;
+    best->kernel = IA_KERNEL_PERSISTENT;
+    best->block = win.block;
+    best->regs_variant = win.minb;
+    best->refill = win.refill;
+    *best_ms = best_t;
     return IA_OK;
 }
 

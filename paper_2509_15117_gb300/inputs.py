@@ -256,21 +256,21 @@ def c1_workload(n_grid: int = 32):
     return [sysd], y0, np.zeros(len(th)), np.zeros(len(th), dtype=np.int32)
 
 
-def c2_systems():
+def c2_systems(t_max_s: float = 1e-3):
     """The 40 (species, energy) systems of the head-on species x energy sweep (D_e = 1 K, q = 0.1)."""
     out = []
     for sp in C2_SPECIES:
         for E_K in C2_ENERGIES_K:
             r0 = r0_rule(SPECIES[sp]["alpha"], kelvin(E_K))
-            out.append((sp, E_K, make_system(sp, De_K=1.0, q=0.1, a=0.0, r0=r0, t_max_s=1e-3, E_K=E_K)))
+            out.append((sp, E_K, make_system(sp, De_K=1.0, q=0.1, a=0.0, r0=r0, t_max_s=t_max_s, E_K=E_K)))
     return out
 
 
-def c2_workload(n_grid: int = 1024, stride: int = 1, offset: int = 0):
+def c2_workload(n_grid: int = 1024, stride: int = 1, offset: int = 0, t_max_s: float = 1e-3):
     """Head-on sweep over 5 species x 8 energies on an n_grid^2 octant grid each; every
     `stride`-th grid point in each direction starting at `offset` (stride 1 = the full grid).
     Trajectories are ordered system by system. Returns (systems, y0, phi0, sys_id)."""
-    systems = c2_systems()
+    systems = c2_systems(t_max_s)
     th, ph = octant_grid(n_grid)
     idx = np.arange(n_grid * n_grid).reshape(n_grid, n_grid)[offset::stride, offset::stride].ravel()
     th, ph = th[idx], ph[idx]
@@ -319,14 +319,14 @@ def c4_cells():
     return cells
 
 
-def c4_workload(scale: float = 1.0, seed: int = 4):
+def c4_workload(scale: float = 1.0, seed: int = 4, t_max_s: float = 1e-3):
     """Mixed-parameter sweep: each cell is its own system; head-on with (theta, phi) uniform on the
     octant surface, random rf phase, E = 1.5 uK. `scale` shrinks every cell (>= 1 trajectory)."""
     systems, ys, ps, sids = [], [], [], []
     E_K = 1.5e-6
     for k, c in enumerate(c4_cells()):
         sysd = make_system(c["species"], De_K=c["De_K"], q=c["q"], a=c["a"], r0=5000.0,
-                           t_max_s=1e-3, E_K=E_K)
+                           t_max_s=t_max_s, E_K=E_K)
         sysd.r0 = r0_rule(sysd.alpha, kelvin(E_K))
         n = max(1, int(round(c["n"] * scale)))
         th, ph = octant_random(n, seed * 1_000_003 + k)

@@ -1,6 +1,8 @@
 """The C-ABI library builds for sm_103a, loads, and exports every function include/ionatom.h declares.
 No compute call is made here (no GPU on the build machine)."""
 import ctypes
+
+import numpy as np
 import os
 import re
 
@@ -70,3 +72,25 @@ def test_invalid_arguments_rejected_without_touching_gpu():
     assert Bd.ia_scratch_bytes(1000, kernel=Bd.IA_KERNEL_PERSISTENT, suspend_capacity=5) == head + 256 + 5 * 256
     with pytest.raises(Bd.IaError):
         Bd.ia_scratch_bytes(10, kernel=Bd.IA_KERNEL_PERSISTENT, tail_group=5)
+
+
+def test_stats_layout_and_host_statistics():
+    from paper_2509_15117_gb300 import statistics as St
+    assert Bd.STATS_DTYPE.itemsize == 8 * (3 + 8 + 32 + 64) + 16
+    rec = np.zeros(1, dtype=Bd.STATS_DTYPE)[0]
+    rec["n"] = 1000
+    rec["n_complex"] = 430
+    rec["sum_dE"] = 2.0
+    rec["sum_dE2"] = 0.01
+    rec["lifetime_hist"][10] = 300
+    rec["lifetime_hist"][20] = 130
+    s = St.summarize(rec)
+    p, lo, hi = s["P_complex"], *s["P_complex_3sigma"]
+    assert p == 0.43 and lo < p < hi
+    # Wilson interval against its closed form at z = 3
+    z, n = 3.0, 1000
+    half = z * np.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / (1 + z * z / n)
+    assert hi - lo == pytest.approx(2 * half, rel=1e-12)
+    assert s["mean_dE_ion"] == pytest.approx(0.002)
+    assert s["survival"][0] == 1.0 and s["survival"][11] == pytest.approx(130 / 430)
+    assert s["survival"][21] == 0.0
