@@ -266,6 +266,43 @@ int ia_graph_destroy(ia_graph* graph);
 int ia_autotune(ia_system* sys, const ia_ic_soa* ic, int64_t n, int32_t attempt_cap, const ia_launch_opts* base,
                 ia_launch_opts* best, double* best_ms, void* stream);
 
+/* ---- tangent (forward-mode) differentiation and FTLE ---- */
+
+/* Tangent seeds: up to 4 directions p_k, each given by d y0 / d p_k per trajectory and by the
+ * derivative of the trap's q vector (same for every trajectory of the launch). */
+typedef struct ia_tangent_in {
+    const double* dy0;      /* device, ndir x 12 x ld: d y0[c] / d p_k of trajectory i at dy0[(k*12 + c)*ld + i] */
+    double dq[4][3];        /* d q_j / d p_k (host values) */
+    int32_t ndir;           /* 1..4 */
+    int32_t reserved;       /* must be 0 */
+    int64_t ld;             /* >= n */
+} ia_tangent_in;
+
+/* Tangent results (device pointers), direction k of trajectory i at [k*ld + i]. */
+typedef struct ia_tangent_out {
+    double* d_theta_s;      /* d theta_s / d p_k */
+    double* d_dp;           /* d |p_f - p_i| / d p_k */
+    double* d_dE_ion;       /* d dE_ion / d p_k */
+    double* d_t_final;      /* d t_final / d p_k */
+    double* dy_final;       /* ndir x 12 x ld: d y_final / d p_k, or NULL */
+    double* ftle;           /* ld: finite-time Lyapunov exponent along direction 0, per a.u. of time, in the
+                               norm with positions in units of r_e and velocities in sqrt(2 D_e/mu);
+                               or NULL */
+    int64_t ld;             /* >= n */
+} ia_tangent_out;
+
+/*
+ * Integrate n trajectories (as ia_launch, same primal results bit for bit) together with the
+ * discrete tangent of the DP5(4) map along up to four directions: step sizes and accept/reject
+ * decisions of the primal are held fixed; the exit time gets its own sensitivity from the
+ * continuous extension (d s_star / d p = -(d . dd/dp) / (d . dd/ds)). Derivatives of theta_s, dp, dE_ion and
+ * t_final follow by the chain rule. No counterpart in the paper's text, which measures chaos through
+ * fractal maps and lifetimes; the FTLE output gives the finite-time Lyapunov exponent for those maps.
+ * One warp per trajectory. Asynchronous on `stream`; uses the system's scratch for a work counter.
+ */
+int ia_launch_tangent(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* out,
+                      const ia_tangent_in* tin, const ia_tangent_out* tout, void* stream);
+
 /*
  * Test hook (no counterpart in the paper): y[i] = 1/x[i] computed as the integrator computes 1/r^2
  * (Newton-Raphson from an FP32 seed). x, y: device arrays of n doubles, x[i] > 0. Asynchronous.

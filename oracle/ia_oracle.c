@@ -628,3 +628,429 @@ void orc_ionatom_segment(const orc_system* s, double phi0, double t0, double t1,
     *n_steps = st.n_steps;
     *n_rej = st.n_rej;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Differentiation along a frozen step sequence (the derivative of the computed map with the     */
+/* accepted step sizes held fixed), used to check the tangent and adjoint kernels.               */
+
+typedef struct {
+    ionatom_obs o;
+    double* hs;
+    int64_t cap, n;
+} steps_obs;
+
+static int record_on_accept(void* vobs, double t_old, const double* y_old, double h, const double* y_new,
+                            double k[7][ORC_N])
+{
+    steps_obs* so = (steps_obs*)vobs;
+    if (so->n < so->cap) so->hs[so->n] = h;
+    so->n += 1;
+    return ionatom_on_accept(&so->o, t_old, y_old, h, y_new, k);
+}
+
+/* orc_trajectory that also records the accepted step sizes (hs, up to cap) and how the trajectory
+ * ended: *mode = 0 crossing inside the last step, 1 otherwise (the end of the last step is final). */
+int64_t orc_trajectory_steps(const orc_system* s, const double* y0, double phi0, orc_result* r, double* hs,
+                             int64_t cap, int32_t* mode)
+{
+    orc_trajectory(s, y0, phi0, r);
+    /* repeat the integration with the recording callback (same arithmetic, same decisions) */
+    double atol[ORC_N];
+    for (int b = 0; b < 4; ++b)
+        for (int j = 0; j < 3; ++j) atol[3 * b + j] = (b % 2 == 0) ? s->atol_pos : s->atol_vel;
+    steps_obs so;
+    memset(&so, 0, sizeof(so));
+    so.o.ctx.sys = s;
+    so.o.ctx.phi0 = phi0;
+    so.o.r0sq = s->r0 * s->r0;
+    so.o.rdot_prev = rdot_times_r(y0);
+    so.hs = hs;
+    so.cap = cap;
+    double y[ORC_N];
+    memcpy(y, y0, sizeof(y));
+    orc_loop_state st;
+    dp5_drive(ionatom_rhs, &so.o.ctx, ORC_N, 0.0, s->t_max, y, s->rtol, atol, s->h_max, 0.0,
+              s->max_attempts, record_on_accept, &so, &st);
+    *mode = (so.o.exited && so.o.exit_flags == 0) ? 0 : 1;
+    return so.n;
+}
+
+/* Jacobian of the right-hand side with respect to y (12 x 12, row-major), from V'(r) and V''(r):
+ * the force on the atom F(d) = -V'(r) d/r has dF/dd = -V'' dd^T/r^2 - (V'/r)(I - dd^T/r^2). */
+static void ionatom_jac(const orc_system* s, double phi0, double t, const double* y, double J[ORC_N][ORC_N])
+{
+    double C4 = sys_C4(s), C8 = sys_C8(s);
+    double d[3];
+    separation(y, d);
+    double r = sqrt(dot3(d, d));
+    double V1 = -8.0 * C8 / pow(r, 9) + 4.0 * C4 / pow(r, 5);
+    double V2 = 72.0 * C8 / pow(r, 10) - 20.0 * C4 / pow(r, 6);
+    double dF[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double nn = d[a] * d[b] / (r * r);
+            dF[a][b] = -V2 * nn - (V1 / r) * ((a == b ? 1.0 : 0.0) - nn);
+        }
+    double cosv = (double)s->rf_sign * cos(s->Omega * t + phi0);
+    memset(J, 0, sizeof(double) * ORC_N * ORC_N);
+    for (int j = 0; j < 3; ++j) {
+        J[0 + j][3 + j] = 1.0;
+        J[6 + j][9 + j] = 1.0;
+        J[3 + j][0 + j] = -(s->Omega * s->Omega / 4.0) * (s->a[j] + 2.0 * s->q[j] * cosv);
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            J[3 + a][0 + b] += dF[a][b] / s->m_ion;   /* d a_ion / d x_ion */
+            J[3 + a][6 + b] += -dF[a][b] / s->m_ion;  /* d a_ion / d x_atom */
+            J[9 + a][6 + b] += dF[a][b] / s->m_atom;  /* d a_atom / d x_atom */
+            J[9 + a][0 + b] += -dF[a][b] / s->m_atom; /* d a_atom / d x_ion */
+        }
+}
+
+/* d f / d q_j (q-vector direction dq): only the ion acceleration depends on q. */
+static void ionatom_dfdq(const orc_system* s, double phi0, double t, const double* y, const double* dq, double* out)
+{
+    double cosv = (double)s->rf_sign * cos(s->Omega * t + phi0);
+    memset(out, 0, sizeof(double) * ORC_N);
+    for (int j = 0; j < 3; ++j) out[3 + j] = -(s->Omega * s->Omega / 4.0) * 2.0 * dq[j] * cosv * y[j];
+}
+
+/* The continuous extension's weights b_j(s) and their s-derivatives. */
+static void dense_weights(double sv, double w[7], double dw[7])
+{
+    for (int j = 0; j < 7; ++j) {
+        w[j] = sv * (DP_BI[j][0] + sv * (DP_BI[j][1] + sv * (DP_BI[j][2] + sv * DP_BI[j][3])));
+        dw[j] = DP_BI[j][0] + sv * (2.0 * DP_BI[j][1] + sv * (3.0 * DP_BI[j][2] + sv * 4.0 * DP_BI[j][3]));
+    }
+}
+
+/* Observables from initial and final states (same definitions as orc_trajectory). */
+static void observables(const orc_system* s, double phi0, const double* y0, const double* yf, double tf, double* obs)
+{
+    const double* v0 = y0 + 9;
+    const double* vf = yf + 9;
+    double cr[3] = {v0[1] * vf[2] - v0[2] * vf[1], v0[2] * vf[0] - v0[0] * vf[2], v0[0] * vf[1] - v0[1] * vf[0]};
+    obs[0] = atan2(sqrt(dot3(cr, cr)), dot3(v0, vf));
+    double dv[3] = {vf[0] - v0[0], vf[1] - v0[1], vf[2] - v0[2]};
+    obs[1] = s->m_atom * sqrt(dot3(dv, dv));
+    obs[2] = ion_energy(s, phi0, tf, yf) - ion_energy(s, phi0, 0.0, y0);
+    obs[3] = tf;
+}
+
+/* Replay of the step sequence hs[0..nh-1] from y0 (fixed steps, no error control). mode 0: the
+ * end is the crossing |d| = r0 located by bisection on the last step's continuous extension,
+ * searched on s in [-0.5, 1.5] (the same polynomial, so small perturbations keep it in that step);
+ * mode 1: the end of the last step. Outputs the observables (theta_s, dp, dE_ion, t_final) and y_f. */
+void orc_replay(const orc_system* s, const double* y0, double phi0, const double* hs, int64_t nh, int32_t mode,
+                double* obs, double* yf)
+{
+    ionatom_ctx c = {s, phi0};
+    double y[ORC_N], k[7][ORC_N], ynew[ORC_N], err[ORC_N];
+    memcpy(y, y0, sizeof(y));
+    double t = 0.0;
+    for (int64_t m = 0; m < nh; ++m) {
+        double h = hs[m];
+        ionatom_rhs(&c, t, y, k[0]);
+        dp5_attempt(ionatom_rhs, &c, ORC_N, t, y, h, k, ynew, err);
+        if (m == nh - 1 && mode == 0) {
+            double lo = -0.5, hi = 1.5, ys[ORC_N], dd[3];
+            for (int it = 0; it < 200; ++it) {
+                double mid = 0.5 * (lo + hi);
+                if (mid <= lo || mid >= hi) break;
+                dp5_dense(ORC_N, y, h, k, mid, ys);
+                separation(ys, dd);
+                if (dot3(dd, dd) - s->r0 * s->r0 < 0.0)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            dp5_dense(ORC_N, y, h, k, hi, yf);
+            observables(s, phi0, y0, yf, t + hi * h, obs);
+            return;
+        }
+        memcpy(y, ynew, sizeof(y));
+        t = t + h;
+    }
+    memcpy(yf, y, sizeof(y));
+    observables(s, phi0, y0, yf, t, obs);
+}
+
+/* Discrete tangent of the replayed map along ndir directions: Y (12 per direction) follows the
+ * stages K_s = J(t_s, y_s) Y_s + (df/dq) dq, Y_s = Y + h sum_l a_sl K_l, Y_new = Y + h sum_l b_l K_l;
+ * at a crossing (mode 0) d s_star / d p = -(d . dY_d) / (d . dd/ds) on the continuous extension and
+ * dy_f = Y(s_star) + (dy/ds) d s_star. The observables are differentiated by hand below.
+ * dy0: ndir x 12; dq: ndir x 3; out: ndir x 4 (theta_s, dp, dE_ion, t_final); dyf: ndir x 12. */
+void orc_tangent(const orc_system* s, const double* y0, double phi0, const double* hs, int64_t nh, int32_t mode,
+                 const double* dy0, const double* dq, int32_t ndir, double* out, double* dyf)
+{
+    ionatom_ctx c = {s, phi0};
+    enum { MAXD = 4 };
+    double y[ORC_N], k[7][ORC_N], ys[ORC_N];
+    double Y[MAXD][ORC_N], K[MAXD][7][ORC_N], Ys[MAXD][ORC_N];
+    double J[ORC_N][ORC_N], fq[ORC_N];
+    memcpy(y, y0, sizeof(y));
+    for (int d = 0; d < ndir; ++d) memcpy(Y[d], dy0 + ORC_N * d, sizeof(double) * ORC_N);
+    double t = 0.0, sstar = 1.0, h = 0.0, tf = 0.0;
+    double yfin[ORC_N], dyfin[MAXD][ORC_N], dtf[MAXD];
+    for (int d = 0; d < ndir; ++d) dtf[d] = 0.0;
+    for (int64_t m = 0; m < nh; ++m) {
+        h = hs[m];
+        /* stages of the primal and of each direction */
+        for (int st = 0; st < 7; ++st) {
+            double tsv = t + DP_C[st] * h;
+            for (int i = 0; i < ORC_N; ++i) {
+                double acc = 0.0;
+                for (int l = 0; l < st; ++l) acc += DP_A[st][l] * k[l][i];
+                ys[i] = y[i] + h * acc;
+            }
+            ionatom_rhs(&c, tsv, ys, k[st]);
+            ionatom_jac(s, phi0, tsv, ys, J);
+            for (int d = 0; d < ndir; ++d) {
+                for (int i = 0; i < ORC_N; ++i) {
+                    double acc = 0.0;
+                    for (int l = 0; l < st; ++l) acc += DP_A[st][l] * K[d][l][i];
+                    Ys[d][i] = Y[d][i] + h * acc;
+                }
+                ionatom_dfdq(s, phi0, tsv, ys, dq + 3 * d, fq);
+                for (int i = 0; i < ORC_N; ++i) {
+                    double acc = fq[i];
+                    for (int jj = 0; jj < ORC_N; ++jj) acc += J[i][jj] * Ys[d][jj];
+                    K[d][st][i] = acc;
+                }
+            }
+        }
+        if (m == nh - 1 && mode == 0) {
+            /* locate the crossing as orc_replay does, then the event sensitivity */
+            double lo = -0.5, hi = 1.5, yt[ORC_N], dd[3];
+            for (int it = 0; it < 200; ++it) {
+                double mid = 0.5 * (lo + hi);
+                if (mid <= lo || mid >= hi) break;
+                dp5_dense(ORC_N, y, h, k, mid, yt);
+                separation(yt, dd);
+                if (dot3(dd, dd) - s->r0 * s->r0 < 0.0)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            sstar = hi;
+            double w[7], dw[7];
+            dense_weights(sstar, w, dw);
+            double ydot[ORC_N];
+            for (int i = 0; i < ORC_N; ++i) {
+                double a1 = 0.0, a2 = 0.0;
+                for (int j = 0; j < 7; ++j) {
+                    a1 += w[j] * k[j][i];
+                    a2 += dw[j] * k[j][i];
+                }
+                yfin[i] = y[i] + h * a1;
+                ydot[i] = h * a2; /* dy/ds */
+            }
+            double df[3], dfs[3];
+            separation(yfin, df);
+            separation(ydot, dfs);
+            for (int d = 0; d < ndir; ++d) {
+                double Yi[ORC_N];
+                for (int i = 0; i < ORC_N; ++i) {
+                    double a1 = 0.0;
+                    for (int j = 0; j < 7; ++j) a1 += w[j] * K[d][j][i];
+                    Yi[i] = Y[d][i] + h * a1;
+                }
+                double dY[3];
+                separation(Yi, dY);
+                double ds = -dot3(df, dY) / dot3(df, dfs);
+                for (int i = 0; i < ORC_N; ++i) dyfin[d][i] = Yi[i] + ydot[i] * ds;
+                dtf[d] = h * ds;
+            }
+            tf = t + sstar * h;
+            goto done;
+        }
+        for (int i = 0; i < ORC_N; ++i) {
+            double acc = 0.0;
+            for (int l = 0; l < 7; ++l) acc += DP_B[l] * k[l][i];
+            y[i] = y[i] + h * acc;
+        }
+        for (int d = 0; d < ndir; ++d)
+            for (int i = 0; i < ORC_N; ++i) {
+                double acc = 0.0;
+                for (int l = 0; l < 7; ++l) acc += DP_B[l] * K[d][l][i];
+                Y[d][i] = Y[d][i] + h * acc;
+            }
+        t = t + h;
+    }
+    memcpy(yfin, y, sizeof(y));
+    for (int d = 0; d < ndir; ++d) memcpy(dyfin[d], Y[d], sizeof(double) * ORC_N);
+    tf = t;
+done:
+    for (int d = 0; d < ndir; ++d) {
+        /* chain rule for the observables (Fig. 1 caption definitions and the ion energy of Eq. 1) */
+        const double* dy0d = dy0 + ORC_N * d;
+        const double* v0 = y0 + 9;
+        const double* vf = yfin + 9;
+        const double* dv0 = dy0d + 9;
+        const double* dvf = dyfin[d] + 9;
+        double cr[3] = {v0[1] * vf[2] - v0[2] * vf[1], v0[2] * vf[0] - v0[0] * vf[2], v0[0] * vf[1] - v0[1] * vf[0]};
+        double dcr[3] = {dv0[1] * vf[2] + v0[1] * dvf[2] - dv0[2] * vf[1] - v0[2] * dvf[1],
+                         dv0[2] * vf[0] + v0[2] * dvf[0] - dv0[0] * vf[2] - v0[0] * dvf[2],
+                         dv0[0] * vf[1] + v0[0] * dvf[1] - dv0[1] * vf[0] - v0[1] * dvf[0]};
+        double C = sqrt(dot3(cr, cr)), D = dot3(v0, vf);
+        double dC = C > 0.0 ? dot3(cr, dcr) / C : 0.0;
+        double dD = dot3(dv0, vf) + dot3(v0, dvf);
+        out[4 * d + 0] = (D * dC - C * dD) / (C * C + D * D);
+        double u[3] = {vf[0] - v0[0], vf[1] - v0[1], vf[2] - v0[2]};
+        double du[3] = {dvf[0] - dv0[0], dvf[1] - dv0[1], dvf[2] - dv0[2]};
+        double un = sqrt(dot3(u, u));
+        out[4 * d + 1] = un > 0.0 ? s->m_atom * dot3(u, du) / un : 0.0;
+        /* E_ion(t, y; q) = m/2 |v_i|^2 + sum_j (m Omega^2/8)(a_j + 2 s q_j cos(Omega t + phi0)) x_j^2 */
+        double W = s->m_ion * s->Omega * s->Omega / 8.0;
+        double sg = (double)s->rf_sign;
+        double cf = cos(s->Omega * tf + phi0), sf = sin(s->Omega * tf + phi0), c0 = cos(phi0);
+        const double* dqd = dq + 3 * d;
+        double e = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            double xf = yfin[j], x0 = y0[j];
+            e += s->m_ion * (yfin[3 + j] * dyfin[d][3 + j] - y0[3 + j] * dy0d[3 + j]);
+            e += 2.0 * W * (s->a[j] + 2.0 * sg * s->q[j] * cf) * xf * dyfin[d][j];
+            e -= 2.0 * W * (s->a[j] + 2.0 * sg * s->q[j] * c0) * x0 * dy0d[j];
+            e += W * 2.0 * sg * s->q[j] * (-s->Omega * sf) * xf * xf * dtf[d];
+            e += W * 2.0 * sg * dqd[j] * (cf * xf * xf - c0 * x0 * x0);
+        }
+        out[4 * d + 2] = e;
+        out[4 * d + 3] = dtf[d];
+        if (dyf) memcpy(dyf + ORC_N * d, dyfin[d], sizeof(double) * ORC_N);
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* The same frozen-step replay in long double (x86: 64-bit mantissa; aarch64: IEEE binary128).  */
+/* Rounding in FP64 is amplified ~10^7 by a bounce, which floors finite differences of the FP64  */
+/* replay near 1e-5; in extended precision they resolve the discrete derivative to ~1e-9.        */
+
+typedef long double ldbl;
+
+static void rhs_ld(const orc_system* s, const ldbl* qv, ldbl phi0, ldbl t, const ldbl* y, ldbl* f)
+{
+    ldbl C4 = 0.5L * (ldbl)s->alpha;
+    ldbl C8 = C4 == 0.0L ? 0.0L : C4 * C4 / (4.0L * (ldbl)s->De);
+    ldbl d[3];
+    for (int j = 0; j < 3; ++j) d[j] = y[6 + j] - y[j];
+    ldbl r = sqrtl(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    ldbl dVdr = -8.0L * C8 / powl(r, 9) + 4.0L * C4 / powl(r, 5);
+    ldbl Om = (ldbl)s->Omega;
+    ldbl cosv = (ldbl)s->rf_sign * cosl(Om * t + phi0);
+    for (int j = 0; j < 3; ++j) {
+        ldbl Fa = -dVdr * d[j] / r;
+        ldbl Ft = -((ldbl)s->m_ion * Om * Om / 4.0L) * ((ldbl)s->a[j] + 2.0L * qv[j] * cosv) * y[j];
+        f[0 + j] = y[3 + j];
+        f[3 + j] = (Ft - Fa) / (ldbl)s->m_ion;
+        f[6 + j] = y[9 + j];
+        f[9 + j] = Fa / (ldbl)s->m_atom;
+    }
+}
+
+static ldbl ion_energy_ld(const orc_system* s, const ldbl* qv, ldbl phi0, ldbl t, const ldbl* y)
+{
+    ldbl Om = (ldbl)s->Omega;
+    ldbl cosv = (ldbl)s->rf_sign * cosl(Om * t + phi0);
+    ldbl E = 0.0L;
+    for (int j = 0; j < 3; ++j) {
+        E += 0.5L * (ldbl)s->m_ion * y[3 + j] * y[3 + j];
+        E += ((ldbl)s->a[j] + 2.0L * qv[j] * cosv) * ((ldbl)s->m_ion * Om * Om / 8.0L) * y[j] * y[j];
+    }
+    return E;
+}
+
+/* Replay from the initial state y0 + eps dy0 with q + eps dq, both formed in extended precision. */
+static void replay_ld(const orc_system* s, const double* y0d, const double* dy0, const double* dq, ldbl eps,
+                      double phi0d, const double* hs, int64_t nh, int32_t mode, double* obs)
+{
+    ldbl y[ORC_N], k[7][ORC_N], ys[ORC_N], y0[ORC_N], qv[3];
+    ldbl phi0 = (ldbl)phi0d;
+    for (int i = 0; i < ORC_N; ++i) y0[i] = y[i] = (ldbl)y0d[i] + eps * (ldbl)dy0[i];
+    for (int j = 0; j < 3; ++j) qv[j] = (ldbl)s->q[j] + eps * (ldbl)dq[j];
+    ldbl t = 0.0L;
+    ldbl yf[ORC_N];
+    ldbl tf = 0.0L;
+    for (int64_t m = 0; m < nh; ++m) {
+        ldbl h = (ldbl)hs[m];
+        rhs_ld(s, qv, phi0, t, y, k[0]);
+        for (int st = 1; st < 7; ++st) {
+            for (int i = 0; i < ORC_N; ++i) {
+                ldbl acc = 0.0L;
+                for (int l = 0; l < st; ++l) acc += (ldbl)DP_A[st][l] * k[l][i];
+                ys[i] = y[i] + h * acc;
+            }
+            rhs_ld(s, qv, phi0, t + (ldbl)DP_C[st] * h, ys, k[st]);
+        }
+        if (m == nh - 1 && mode == 0) {
+            ldbl lo = -0.5L, hi = 1.5L, r0sq = (ldbl)s->r0 * (ldbl)s->r0;
+            for (int it = 0; it < 400; ++it) {
+                ldbl mid = 0.5L * (lo + hi);
+                if (mid <= lo || mid >= hi) break;
+                ldbl d2 = 0.0L;
+                for (int j = 0; j < 3; ++j) {
+                    ldbl pa = 0.0L, pi = 0.0L;
+                    for (int jj = 0; jj < 7; ++jj) {
+                        ldbl w = mid * ((ldbl)DP_BI[jj][0] + mid * ((ldbl)DP_BI[jj][1] + mid * ((ldbl)DP_BI[jj][2] +
+                                        mid * (ldbl)DP_BI[jj][3])));
+                        pa += w * k[jj][6 + j];
+                        pi += w * k[jj][j];
+                    }
+                    ldbl dj = (y[6 + j] + h * pa) - (y[j] + h * pi);
+                    d2 += dj * dj;
+                }
+                if (d2 - r0sq < 0.0L)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            for (int i = 0; i < ORC_N; ++i) {
+                ldbl acc = 0.0L;
+                for (int jj = 0; jj < 7; ++jj) {
+                    ldbl w = hi * ((ldbl)DP_BI[jj][0] + hi * ((ldbl)DP_BI[jj][1] + hi * ((ldbl)DP_BI[jj][2] +
+                                   hi * (ldbl)DP_BI[jj][3])));
+                    acc += w * k[jj][i];
+                }
+                yf[i] = y[i] + h * acc;
+            }
+            tf = t + hi * h;
+            goto done;
+        }
+        for (int i = 0; i < ORC_N; ++i) {
+            ldbl acc = 0.0L;
+            for (int l = 0; l < 7; ++l) acc += (ldbl)DP_B[l] * k[l][i];
+            y[i] = y[i] + h * acc;
+        }
+        t = t + h;
+    }
+    for (int i = 0; i < ORC_N; ++i) yf[i] = y[i];
+    tf = t;
+done:
+    {
+        const ldbl* v0 = y0 + 9;
+        const ldbl* vf = yf + 9;
+        ldbl cr[3] = {v0[1] * vf[2] - v0[2] * vf[1], v0[2] * vf[0] - v0[0] * vf[2], v0[0] * vf[1] - v0[1] * vf[0]};
+        obs[0] = (double)atan2l(sqrtl(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]),
+                                v0[0] * vf[0] + v0[1] * vf[1] + v0[2] * vf[2]);
+        ldbl dv[3] = {vf[0] - v0[0], vf[1] - v0[1], vf[2] - v0[2]};
+        obs[1] = (double)((ldbl)s->m_atom * sqrtl(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]));
+        obs[2] = (double)(ion_energy_ld(s, qv, phi0, tf, yf) - ion_energy_ld(s, qv, phi0, 0.0L, y0));
+        obs[3] = (double)tf;
+    }
+}
+
+/* Central differences of the extended-precision replay along direction (dy0, dq), with the
+ * perturbed initial state and q formed in extended precision; Richardson-combined spacings delta
+ * and delta/2 (truncation O(delta^4)). out: derivatives of (theta_s, dp, dE_ion, t_final). */
+void orc_fd_ld(const orc_system* s, const double* y0, double phi0, const double* hs, int64_t nh, int32_t mode,
+               const double* dy0, const double* dq, double delta, double* out)
+{
+    double D[2][4];
+    for (int pass = 0; pass < 2; ++pass) {
+        double dl = pass == 0 ? delta : 0.5 * delta;
+        double op[4], om[4];
+        replay_ld(s, y0, dy0, dq, (ldbl)dl, phi0, hs, nh, mode, op);
+        replay_ld(s, y0, dy0, dq, -(ldbl)dl, phi0, hs, nh, mode, om);
+        for (int o = 0; o < 4; ++o) D[pass][o] = (op[o] - om[o]) / (2.0 * dl);
+    }
+    for (int o = 0; o < 4; ++o) out[o] = (4.0 * D[1][o] - D[0][o]) / 3.0;
+}

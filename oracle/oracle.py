@@ -217,3 +217,76 @@ def ionatom_segment(desc: dict, phi0: float, t0: float, t1: float, y0):
     nr = ctypes.c_int64()
     lib().orc_ionatom_segment(ctypes.byref(s), phi0, t0, t1, _dptr(y), ctypes.byref(ns), ctypes.byref(nr))
     return y, ns.value, nr.value
+
+
+def trajectory_steps(desc: dict, y0, phi0: float, cap: int = 5_000_000):
+    """Run one trajectory and return (result record, accepted step sizes, end mode)."""
+    L = lib()
+    s = make_system(desc)
+    y = np.ascontiguousarray(y0, dtype=np.float64)
+    hs = np.zeros(cap)
+    res = np.zeros(1, dtype=RESULT_DTYPE)
+    mode = ctypes.c_int32()
+    L.orc_trajectory_steps.restype = ctypes.c_int64
+    L.orc_trajectory_steps.argtypes = [ctypes.POINTER(OrcSystem), ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                       ctypes.POINTER(OrcResult), ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                                       ctypes.POINTER(ctypes.c_int32)]
+    n = L.orc_trajectory_steps(ctypes.byref(s), _dptr(y), phi0, res.ctypes.data_as(ctypes.POINTER(OrcResult)),
+                               _dptr(hs), cap, ctypes.byref(mode))
+    assert n <= cap
+    return res[0], hs[:n].copy(), int(mode.value)
+
+
+def replay(desc: dict, y0, phi0: float, hs, mode: int):
+    """Fixed-step replay of an accepted step sequence; returns (observables[4], y_final[12])."""
+    L = lib()
+    s = make_system(desc)
+    y = np.ascontiguousarray(y0, dtype=np.float64)
+    hs = np.ascontiguousarray(hs, dtype=np.float64)
+    obs = np.zeros(4)
+    yf = np.zeros(12)
+    L.orc_replay.argtypes = [ctypes.POINTER(OrcSystem), ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                             ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_int32,
+                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.orc_replay(ctypes.byref(s), _dptr(y), phi0, _dptr(hs), len(hs), mode, _dptr(obs), _dptr(yf))
+    return obs, yf
+
+
+def tangent(desc: dict, y0, phi0: float, hs, mode: int, dy0, dq):
+    """Discrete tangent along the frozen step sequence; dy0 (ndir, 12), dq (ndir, 3).
+    Returns (out (ndir, 4): d theta_s, d dp, d dE_ion, d t_final; dy_final (ndir, 12))."""
+    L = lib()
+    s = make_system(desc)
+    y = np.ascontiguousarray(y0, dtype=np.float64)
+    hs = np.ascontiguousarray(hs, dtype=np.float64)
+    dy0 = np.ascontiguousarray(dy0, dtype=np.float64)
+    dq = np.ascontiguousarray(dq, dtype=np.float64)
+    nd = dy0.shape[0]
+    out = np.zeros((nd, 4))
+    dyf = np.zeros((nd, 12))
+    L.orc_tangent.argtypes = [ctypes.POINTER(OrcSystem), ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                              ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_int32,
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.orc_tangent(ctypes.byref(s), _dptr(y), phi0, _dptr(hs), len(hs), mode, _dptr(dy0), _dptr(dq), nd,
+                  _dptr(out), _dptr(dyf))
+    return out, dyf
+
+
+def fd_extended(desc: dict, y0, phi0: float, hs, mode: int, dy0, dq, delta: float):
+    """Richardson-combined central differences of the extended-precision frozen-step replay along
+    one direction (dy0 (12,), dq (3,)); returns d(theta_s, dp, dE_ion, t_final)."""
+    L = lib()
+    s = make_system(desc)
+    y = np.ascontiguousarray(y0, dtype=np.float64)
+    hs = np.ascontiguousarray(hs, dtype=np.float64)
+    d1 = np.ascontiguousarray(dy0, dtype=np.float64)
+    d2 = np.ascontiguousarray(dq, dtype=np.float64)
+    out = np.zeros(4)
+    L.orc_fd_ld.argtypes = [ctypes.POINTER(OrcSystem), ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                            ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_int32,
+                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                            ctypes.POINTER(ctypes.c_double)]
+    L.orc_fd_ld(ctypes.byref(s), _dptr(y), phi0, _dptr(hs), len(hs), mode, _dptr(d1), _dptr(d2), delta,
+                _dptr(out))
+    return out

@@ -31,7 +31,7 @@ ST_COMPLEX = 1 << 8
 
 EXPORTED = ("ia_system_create", "ia_system_destroy", "ia_system_count", "ia_scratch_bytes", "ia_reserve",
             "ia_launch", "ia_launch_static", "ia_reduce_stats", "ia_reserve_stats", "ia_graph_create",
-            "ia_graph_launch", "ia_graph_destroy", "ia_autotune", "ia_fp64_peak", "ia_rcp_check",
+            "ia_graph_launch", "ia_graph_destroy", "ia_autotune", "ia_launch_tangent", "ia_fp64_peak", "ia_rcp_check",
             "ia_error_string", "ia_version")
 
 STATS_BOUNCE_BINS = 32
@@ -84,6 +84,17 @@ class ia_launch_opts(ctypes.Structure):
                 ("scratch", ctypes.c_void_p), ("scratch_bytes", ctypes.c_int64)]
 
 
+class ia_tangent_in(ctypes.Structure):
+    _fields_ = [("dy0", ctypes.c_void_p), ("dq", (ctypes.c_double * 3) * 4), ("ndir", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("ld", ctypes.c_int64)]
+
+
+class ia_tangent_out(ctypes.Structure):
+    _fields_ = [("d_theta_s", ctypes.c_void_p), ("d_dp", ctypes.c_void_p), ("d_dE_ion", ctypes.c_void_p),
+                ("d_t_final", ctypes.c_void_p), ("dy_final", ctypes.c_void_p), ("ftle", ctypes.c_void_p),
+                ("ld", ctypes.c_int64)]
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -128,6 +139,9 @@ def load(build_if_missing: bool = True):
     L.ia_autotune.argtypes = [ctypes.c_void_p, P(ia_ic_soa), ctypes.c_int64, ctypes.c_int32, P(ia_launch_opts),
                               P(ia_launch_opts), P(ctypes.c_double), ctypes.c_void_p]
     L.ia_autotune.restype = ctypes.c_int
+    L.ia_launch_tangent.argtypes = [ctypes.c_void_p, P(ia_ic_soa), ctypes.c_int64, P(ia_obs_soa),
+                                    P(ia_tangent_in), P(ia_tangent_out), ctypes.c_void_p]
+    L.ia_launch_tangent.restype = ctypes.c_int
     L.ia_scratch_bytes.argtypes = [ctypes.c_int64, P(ia_launch_opts)]
     L.ia_scratch_bytes.restype = ctypes.c_int64
     L.ia_reserve.argtypes = [ctypes.c_void_p, ctypes.c_int64, P(ia_launch_opts)]
@@ -370,6 +384,44 @@ def ia_autotune(handle: int, y0_soa, phi0, sys_id, attempt_cap: int = 1024, orde
     _check(load().ia_autotune(handle, ctypes.byref(ic), n, attempt_cap, ctypes.byref(b), ctypes.byref(best),
                               ctypes.byref(ms), _stream_ptr(stream)))
     return {"block": best.block, "regs_variant": best.regs_variant, "refill": best.refill}, ms.value
+
+
+def alloc_tangent(n: int, ndir: int, dy_final: bool = False, ftle: bool = True, device="cuda") -> dict:
+    import torch
+    t = {k: torch.empty((ndir, n), dtype=torch.float64, device=device)
+         for k in ("d_theta_s", "d_dp", "d_dE_ion", "d_t_final")}
+    if dy_final:
+        t["dy_final"] = torch.empty((ndir, 12, n), dtype=torch.float64, device=device)
+    if ftle:
+        t["ftle"] = torch.empty(n, dtype=torch.float64, device=device)
+    return t
+
+
+def ia_launch_tangent(handle: int, y0_soa, phi0, sys_id, out: dict, dy0, dq, tan: dict, stream=None) -> None:
+    """Tangent launch: dy0 (ndir, 12, n) device float64 (d y0 / d p_k), dq (ndir, 3) host (d q / d p_k)."""
+    n = int(phi0.shape[0])
+    ic = _ic_struct(y0_soa, phi0, sys_id, None)
+    o = _obs_struct(out, n)
+    ti = ia_tangent_in()
+    ndir = int(dy0.shape[0])
+    ti.dy0 = dy0.data_ptr()
+    dq = np.asarray(dq, dtype=np.float64)
+    for k in range(ndir):
+        for j in range(3):
+            ti.dq[k][j] = float(dq[k, j])
+    ti.ndir = ndir
+    ti.reserved = 0
+    ti.ld = n
+    to = ia_tangent_out()
+    to.d_theta_s = tan["d_theta_s"].data_ptr()
+    to.d_dp = tan["d_dp"].data_ptr()
+    to.d_dE_ion = tan["d_dE_ion"].data_ptr()
+    to.d_t_final = tan["d_t_final"].data_ptr()
+    to.dy_final = tan["dy_final"].data_ptr() if "dy_final" in tan else None
+    to.ftle = tan["ftle"].data_ptr() if "ftle" in tan else None
+    to.ld = n
+    _check(load().ia_launch_tangent(handle, ctypes.byref(ic), n, ctypes.byref(o), ctypes.byref(ti), ctypes.byref(to),
+                                    _stream_ptr(stream)))
 
 
 class System:

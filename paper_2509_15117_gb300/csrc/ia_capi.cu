@@ -25,6 +25,7 @@
 
 #include "ia_traj.cuh"
 #include "ia_stats.cuh"
+#include "ia_tangent.cuh"
 #include "../../include/ionatom.h"
 
 using namespace ia;
@@ -427,6 +428,321 @@ __global__ void __launch_bounds__(128) k_tail(const SysDev* __restrict__ tab, Ic
     tail_phase<G>(tab, ic, out, susp, ready, ctr, cap, false, 0ull);
 }
 
+
+// Tangent kernel: one trajectory per warp (lane = direction x 6 + component); see ia_tangent.cuh.
+__global__ void __launch_bounds__(128) k_tangent(const SysDev* __restrict__ tab, int n_sys, IcPtrs ic, ObsPtrs out,
+                                                 long long n, TanIn tin, TanOut tout,
+                                                 unsigned long long* __restrict__ work)
+{
+    const TLane tl = tlane();
+    const int lane = threadIdx.x & 31;
+    const int yi = tl.comp < 3 ? tl.comp : tl.comp + 3;  // position index in y
+    const int yv = yi + 3;                              // velocity index
+    const int dsel = tl.dir - 1;                         // tangent direction of this lane, -1: primal
+    const bool used = tl.dir <= tin.ndir;
+    for (;;) {
+        unsigned long long claim = 0;
+        if (lane == 0) claim = atomicAdd(work, 1ull);
+        claim = __shfl_sync(FULL, claim, 0);
+        if (claim >= (unsigned long long)n) break;
+        const long long i = (long long)claim;
+        const int sid = ic.sys_id ? __ldg(ic.sys_id + i) : 0;
+        if (sid < 0 || sid >= n_sys) {
+            if (lane == 0) store_bad_sid(ic, out, tab, i);
+            if (lane < tin.ndir) {
+                const long long o = (long long)lane * tout.ld + i;
+                tout.d_theta[o] = 0.0; tout.d_dp[o] = 0.0; tout.d_dE[o] = 0.0; tout.d_tf[o] = 0.0;
+            }
+            if (tout.ftle && lane == 0) tout.ftle[i] = 0.0;
+            continue;
+        }
+        const SysDev& P = tab[sid];
+        double x, v;
+        if (tl.dir == 0) {
+            x = __ldg(ic.y0 + yi * ic.ld + i);
+            v = __ldg(ic.y0 + yv * ic.ld + i);
+        } else if (used) {
+            x = __ldg(tin.dy0 + ((long long)dsel * 12 + yi) * tin.ld + i);
+            v = __ldg(tin.dy0 + ((long long)dsel * 12 + yv) * tin.ld + i);
+        } else {
+            x = 0.0;
+            v = 0.0;
+        }
+        Scal S;
+        S.phi0 = __ldg(ic.phi0 + i);
+        // the primal state must be usable (same test as lane mode)
+        bool okl = tl.dir != 0 || (is_finite(x) && is_finite(v));
+        const bool ok_state = __all_sync(FULL, okl) && is_finite(S.phi0);
+        double xs[6], vs[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            xs[k] = shfl(x, k);
+            vs[k] = shfl(v, k);
+        }
+        double dd0 = xs[3] - xs[0], dd1 = xs[4] - xs[1], dd2 = xs[5] - xs[2];
+        const double r2init = fma(dd0, dd0, fma(dd1, dd1, dd2 * dd2));
+        if (!ok_state || !(dbits(r2init) > 0)) {
+            if (lane == 0) {
+                Final fin;
+                for (int k = 0; k < 3; ++k) {
+                    fin.xi[k] = xs[k]; fin.xa[k] = xs[3 + k]; fin.vi[k] = vs[k]; fin.va[k] = vs[3 + k];
+                }
+                fin.t = 0.0;
+                fin.s_exit = -1.0;
+                fin.status = ST_BAD_IC;
+                store_result(P, ic, out, i, tally(S), fin, false);
+            }
+            if (lane < tin.ndir) {
+                const long long o = (long long)lane * tout.ld + i;
+                tout.d_theta[o] = 0.0; tout.d_dp[o] = 0.0; tout.d_dE[o] = 0.0; tout.d_tf[o] = 0.0;
+            }
+            if (tout.ftle && lane == 0) tout.ftle[i] = 0.0;
+            continue;
+        }
+        // per-lane constants
+        const double kq = tl.comp < 3 ? P.kq[tl.comp] : 0.0;
+        const double ka = tl.comp < 3 ? P.ka[tl.comp] : 0.0;
+        const double coef = tl.comp < 3 ? P.neg_inv_mi : P.inv_ma;
+        double dq_lane = (tl.dir > 0 && used && tl.comp < 3) ? tin.dq[dsel][tl.comp] : 0.0;
+        double dkq = P.kq_per_q * dq_lane;
+        int scale_e = 0;
+        // initial acceleration (FSAL) of primal and tangents, and the initial step of ode45
+        double r2, d3[3];
+        double a1 = tan_accel(P, tl, x, cos(S.phi0), kq, ka, dkq, coef, r2, d3);
+        {
+            Lane L0;
+            for (int k = 0; k < 3; ++k) {
+                L0.xi[k] = xs[k]; L0.xa[k] = xs[3 + k]; L0.vi[k] = vs[k]; L0.va[k] = vs[3 + k];
+                L0.a1i[k] = shfl(a1, k);
+                L0.a1a[k] = shfl(a1, 3 + k);
+            }
+            S.h = initial_step(P, L0);
+        }
+        S.rdot_prev = fma(dd0, vs[3] - vs[0], fma(dd1, vs[4] - vs[1], dd2 * (vs[5] - vs[2])));
+        S.t = 0.0; S.hmin = 0.0; S.t_first = 0.0; S.t_last = 0.0;
+        S.n_acc = 0; S.n_rej = 0; S.n_bounce = 0; S.nofailed = true; S.retry = false;
+        // |Y0| of direction 1 in the FTLE norm
+        double ynorm0 = 0.0;
+        {
+            const double sx = x * P.inv_len, sv = v * P.inv_vel;
+            double part = fma(sx, sx, sv * sv);
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc += __shfl_sync(FULL, part, 6 + k);
+            ynorm0 = sqrt(acc);
+        }
+        Final fin;
+        fin.s_exit = -1.0;
+        int res = 0;
+        uint32_t st = 0xffffffffu;
+        double h = 0.0, t = 0.0;
+        double a3 = 0.0, a4 = 0.0, a5 = 0.0, a6 = 0.0, a7 = 0.0, xn = 0.0, vn = 0.0, r2new = 0.0, dn[3] = {0, 0, 0};
+        Coef K;
+        for (;;) {
+            st = attempt_begin(P, S);
+            if (st != 0xffffffffu) {
+                res = 1;
+                break;
+            }
+            h = S.h;
+            t = S.t;
+            K.h2 = h * h;
+            // coefficients: lane k computes coefficient k (and k + 30 for lanes 0..3)
+            const int k0 = lane < N_COEF ? lane : N_COEF - 1;
+            const double cv0 = COEF_K[k0] * (COEF_H2[k0] ? K.h2 : h);
+            const int k1 = lane + 32 < N_COEF ? lane + 32 : N_COEF - 1;
+            const double cv1 = COEF_K[k1] * (COEF_H2[k1] ? K.h2 : h);
+            {
+                double* kp = &K.c2;
+#pragma unroll
+                for (int k = 0; k < N_COEF; ++k) kp[k] = k < 32 ? shfl(cv0, k) : shfl(cv1, k - 32);
+            }
+            const double chsel = lane < 4 ? cv0 : h;
+            const double cl = cos(fma(P.Omega, t + chsel, S.phi0));
+            const double cs2 = shfl(cl, 0), cs3 = shfl(cl, 1), cs4 = shfl(cl, 2), cs5 = shfl(cl, 3), cs67 = shfl(cl, 4);
+            const double a2 = tan_accel(P, tl, pos2(K, x, v), cs2, kq, ka, dkq, coef, r2, d3);
+            a3 = tan_accel(P, tl, pos3(K, x, v, a1), cs3, kq, ka, dkq, coef, r2, d3);
+            a4 = tan_accel(P, tl, pos4(K, x, v, a1, a2), cs4, kq, ka, dkq, coef, r2, d3);
+            a5 = tan_accel(P, tl, pos5(K, x, v, a1, a2, a3), cs5, kq, ka, dkq, coef, r2, d3);
+            a6 = tan_accel(P, tl, pos6(K, h, x, v, a1, a2, a3, a4), cs67, kq, ka, dkq, coef, r2, d3);
+            xn = pos7(K, h, x, v, a1, a3, a4, a5);
+            a7 = tan_accel(P, tl, xn, cs67, kq, ka, dkq, coef, r2new, dn);
+            vn = vel_new(K, v, a1, a3, a4, a5, a6);
+            // error test on the primal lanes
+            bool okx, fx, okv, fv;
+            float rx, rv;
+            err_check(P.rtol, P.atol_pos, x, xn, err_x(K, a1, a3, a4, a5, a6), okx, fx, rx);
+            err_check(P.rtol, P.atol_vel, v, vn, err_v(K, a1, a3, a4, a5, a6, a7), okv, fv, rv);
+            const bool prim = tl.dir == 0;
+            const bool accept = (__ballot_sync(FULL, prim && !(okx && okv)) & 0x3fu) == 0;
+            const bool finite = (__ballot_sync(FULL, prim && !(fx && fv)) & 0x3fu) == 0;
+            const float ratio = prim ? fmaxf(rx, rv) : 0.0f;
+            float errf = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) errf = fmaxf(errf, __shfl_sync(FULL, ratio, k));
+            const int jj = tl.comp < 3 ? tl.comp : tl.comp - 3;
+            const double wj = shfl(vn, 3 + jj) - shfl(vn, jj);
+            const double w0 = shfl(wj, 0), w1 = shfl(wj, 1), w2 = shfl(wj, 2);
+            const double rd = fma(dn[0], w0, fma(dn[1], w1, dn[2] * w2));
+            if (!finite) {
+                st = ST_NONFINITE;
+                res = 1;
+                break;
+            }
+            if (!accept) {
+                st = on_reject(P, S, errf);
+                if (st != 0xffffffffu) {
+                    res = 1;
+                    break;
+                }
+                continue;
+            }
+            if (on_accept(P, S, rd, r2new)) {
+                res = 2;
+                break;
+            }
+            x = xn;
+            v = vn;
+            a1 = a7;
+            on_commit(P, S, errf);
+            // exact power-of-two rescaling of a tangent direction that left [2^-256, 2^256]
+            int me = max_exp3(x, v, a1);
+#pragma unroll
+            for (int k = 1; k < 6; ++k) me = max(me, __shfl_sync(FULL, me, tl.base + ((tl.comp + k) % 6)));
+            if (tl.dir > 0 && (me > 1023 + 256 || (me > 0 && me < 1023 - 256))) {
+                const int sh = me > 1023 + 256 ? -256 : 256;
+                const double f = sh < 0 ? 0x1p-256 : 0x1p+256;
+                x *= f; v *= f; a1 *= f; dq_lane *= f; dkq *= f;
+                scale_e -= sh;
+            }
+        }
+        // final state of primal (lane 0 owns the epilogue) and of each tangent direction
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            fin.xi[k] = shfl(x, k); fin.xa[k] = shfl(x, 3 + k);
+            fin.vi[k] = shfl(v, k); fin.va[k] = shfl(v, 3 + k);
+        }
+        fin.t = S.t;
+        fin.status = st;
+        double yfx = x, yfv = v;  // this lane's final component (stops: the current state)
+        double dtf_lane = 0.0;
+        if (res == 2) {
+            StepData D;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                D.xi[k] = fin.xi[k]; D.xa[k] = fin.xa[k]; D.vi[k] = fin.vi[k]; D.va[k] = fin.va[k];
+                D.a1i[k] = shfl(a1, k); D.a1a[k] = shfl(a1, 3 + k);
+                D.a3i[k] = shfl(a3, k); D.a3a[k] = shfl(a3, 3 + k);
+                D.a4i[k] = shfl(a4, k); D.a4a[k] = shfl(a4, 3 + k);
+                D.a5i[k] = shfl(a5, k); D.a5a[k] = shfl(a5, 3 + k);
+                D.a6i[k] = shfl(a6, k); D.a6a[k] = shfl(a6, 3 + k);
+                D.a7i[k] = shfl(a7, k); D.a7a[k] = shfl(a7, 3 + k);
+                D.xni[k] = shfl(xn, k); D.xna[k] = shfl(xn, 3 + k);
+                D.vni[k] = shfl(vn, k); D.vna[k] = shfl(vn, 3 + k);
+            }
+            D.h = h;
+            D.t = t;
+            if (lane == 0) finish_exit(P, D, r2new, fin);
+            fin.t = __shfl_sync(FULL, fin.t, 0);
+            fin.s_exit = __shfl_sync(FULL, fin.s_exit, 0);
+            fin.status = __shfl_sync(FULL, fin.status, 0);
+            if (fin.s_exit >= 0.0) {
+                // continuous extension at s* for every lane, and its s-derivative
+                const double s = fin.s_exit, s2 = s * s, h2 = h * h, sh = s * h;
+                const double px1 = s2 * fma(s, fma(s, DP_PX14, DP_PX13), DP_PX12);
+                const double px3 = s2 * fma(s, fma(s, DP_PX34, DP_PX33), DP_PX32);
+                const double px4 = s2 * fma(s, fma(s, DP_PX44, DP_PX43), DP_PX42);
+                const double px5 = s2 * fma(s, fma(s, DP_PX54, DP_PX53), DP_PX52);
+                const double px6 = s2 * fma(s, fma(s, DP_PX64, DP_PX63), DP_PX62);
+                const double b1 = s * fma(s, fma(s, fma(s, DP_BI14, DP_BI13), DP_BI12), DP_BI11);
+                const double b3 = s2 * fma(s, fma(s, DP_BI34, DP_BI33), DP_BI32);
+                const double b4 = s2 * fma(s, fma(s, DP_BI44, DP_BI43), DP_BI42);
+                const double b5 = s2 * fma(s, fma(s, DP_BI54, DP_BI53), DP_BI52);
+                const double b6 = s2 * fma(s, fma(s, DP_BI64, DP_BI63), DP_BI62);
+                const double b7 = s2 * fma(s, fma(s, DP_BI74, DP_BI73), DP_BI72);
+                const double qx = fma(px6, a6, fma(px5, a5, fma(px4, a4, fma(px3, a3, px1 * a1))));
+                const double ux = fma(b7, a7, fma(b6, a6, fma(b5, a5, fma(b4, a4, fma(b3, a3, b1 * a1)))));
+                yfx = fma(h2, qx, fma(sh, v, x));
+                yfv = fma(h, ux, v);
+                // d/ds of the extension (primal lanes use it)
+                const double dp1 = s * fma(s, 4.0 * DP_PX14, 3.0 * DP_PX13) + 2.0 * DP_PX12;
+                const double dp3 = s * fma(s, 4.0 * DP_PX34, 3.0 * DP_PX33) + 2.0 * DP_PX32;
+                const double dp4 = s * fma(s, 4.0 * DP_PX44, 3.0 * DP_PX43) + 2.0 * DP_PX42;
+                const double dp5 = s * fma(s, 4.0 * DP_PX54, 3.0 * DP_PX53) + 2.0 * DP_PX52;
+                const double dp6 = s * fma(s, 4.0 * DP_PX64, 3.0 * DP_PX63) + 2.0 * DP_PX62;
+                const double db1 = fma(s, fma(s, 4.0 * DP_BI14, 3.0 * DP_BI13), 2.0 * DP_BI12) * s + DP_BI11;
+                const double db3 = s * fma(s, 4.0 * DP_BI34, 3.0 * DP_BI33) + 2.0 * DP_BI32;
+                const double db4 = s * fma(s, 4.0 * DP_BI44, 3.0 * DP_BI43) + 2.0 * DP_BI42;
+                const double db5 = s * fma(s, 4.0 * DP_BI54, 3.0 * DP_BI53) + 2.0 * DP_BI52;
+                const double db6 = s * fma(s, 4.0 * DP_BI64, 3.0 * DP_BI63) + 2.0 * DP_BI62;
+                const double db7 = s * fma(s, 4.0 * DP_BI74, 3.0 * DP_BI73) + 2.0 * DP_BI72;
+                const double dqx = s * (dp1 * a1 + dp3 * a3 + dp4 * a4 + dp5 * a5 + dp6 * a6);
+                const double dux = db1 * a1 + s * (db3 * a3 + db4 * a4 + db5 * a5 + db6 * a6 + db7 * a7);
+                const double ysx = fma(h, v, h2 * dqx);  // dx/ds
+                const double ysv = h * dux;              // dv/ds
+                // primal separation and its s-derivative; this direction's separation tangent
+                const int j = tl.comp < 3 ? tl.comp : tl.comp - 3;
+                const double dprim = shfl(yfx, 3 + j) - shfl(yfx, j);
+                const double dsep = shfl(ysx, 3 + j) - shfl(ysx, j);
+                const double dtan = shfl(yfx, tl.base + 3 + j) - shfl(yfx, tl.base + j);
+                const double num = shfl(dprim, 0) * shfl(dtan, tl.base + 0) + shfl(dprim, 1) * shfl(dtan, tl.base + 1) +
+                                   shfl(dprim, 2) * shfl(dtan, tl.base + 2);
+                const double den = shfl(dprim, 0) * shfl(dsep, 0) + shfl(dprim, 1) * shfl(dsep, 1) +
+                                   shfl(dprim, 2) * shfl(dsep, 2);
+                const double dsstar = tl.dir == 0 ? 0.0 : -num / den;
+                const double pysx = shfl(ysx, tl.comp), pysv = shfl(ysv, tl.comp);
+                if (tl.dir > 0) {
+                    yfx = fma(pysx, dsstar, yfx);
+                    yfv = fma(pysv, dsstar, yfv);
+                }
+                dtf_lane = h * dsstar;
+            } else {
+                yfx = xn;  // ends outside r0 without a crossing: the step end is final
+                yfv = vn;
+            }
+        }
+        // primal observables (lane 0) and the derivatives of direction k (lane 6k)
+        double yf[12], dyf[12];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int pi = k < 3 ? k : k + 3;
+            yf[pi] = shfl(yfx, k);
+            yf[pi + 3] = shfl(yfv, k);
+            dyf[pi] = shfl(yfx, tl.base + k);
+            dyf[pi + 3] = shfl(yfv, tl.base + k);
+        }
+        if (lane == 0) store_result(P, ic, out, i, tally(S), fin, true);
+        if (tl.dir > 0 && used && tl.comp == 0) {
+            double y0v[12], dy0v[12], dqv[3];
+            const double sc = ldexp(1.0, -scale_e);
+            for (int c = 0; c < 12; ++c) {
+                y0v[c] = __ldg(ic.y0 + c * ic.ld + i);
+                dy0v[c] = sc * __ldg(tin.dy0 + ((long long)dsel * 12 + c) * tin.ld + i);
+            }
+            for (int c = 0; c < 3; ++c) dqv[c] = sc * tin.dq[dsel][c];
+            double dth, ddp, dde;
+            obs_derivs(P, S.phi0, y0v, yf, fin.t, dy0v, dyf, dtf_lane, dqv, dth, ddp, dde);
+            const long long o = (long long)dsel * tout.ld + i;
+            tout.d_theta[o] = ldexp(dth, scale_e);
+            tout.d_dp[o] = ldexp(ddp, scale_e);
+            tout.d_dE[o] = ldexp(dde, scale_e);
+            tout.d_tf[o] = ldexp(dtf_lane, scale_e);
+            if (tout.dy_final)
+                for (int c = 0; c < 12; ++c) tout.dy_final[((long long)dsel * 12 + c) * tout.ld + i] = ldexp(dyf[c], scale_e);
+            if (tout.ftle && dsel == 0) {
+                double acc = 0.0;
+                for (int c = 0; c < 12; ++c) {
+                    const bool vel = (c % 6) >= 3;
+                    const double z = dyf[c] * (vel ? P.inv_vel : P.inv_len);
+                    acc = fma(z, z, acc);
+                }
+                const double lf = 0.5 * log(acc) + (double)scale_e * 0.69314718055994531;
+                tout.ftle[i] = fin.t > 0.0 && ynorm0 > 0.0 ? (lf - log(ynorm0)) / fin.t : 0.0;
+            }
+        }
+    }
+}
+
 __global__ void k_fp64_fma(double* out, int iters, double a, double b)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -516,6 +832,11 @@ SysDev derive(const ia_system_desc& d)
     P.thr_vel = d.atol_vel / d.rtol;
     P.hinit_den = 0.8 * std::pow(d.rtol, 0.2);
     P.max_attempts = (long long)d.max_attempts;
+    P.kq_per_q = -(W2 / 4.0) * (2.0 * (double)d.rf_sign);
+    P.uq_per_q = (d.m_ion * W2 / 8.0) * (2.0 * (double)d.rf_sign);
+    const double mu = d.m_ion * d.m_atom / (d.m_ion + d.m_atom);
+    P.inv_len = C4 > 0.0 ? 1.0 / std::pow(C4 / (2.0 * d.De), 0.25) : 1.0;
+    P.inv_vel = C4 > 0.0 ? 1.0 / std::sqrt(2.0 * d.De / mu) : 1.0;
     return P;
 }
 
@@ -974,6 +1295,55 @@ int ia_autotune(ia_system* sys, const ia_ic_soa* ic, int64_t n, int32_t attempt_
     best->refill = win.refill;
     *best_ms = best_t;
     return IA_OK;
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Tangent launch
+
+int ia_launch_tangent(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* out,
+                      const ia_tangent_in* tin, const ia_tangent_out* tout, void* stream)
+{
+    if (!sys || !ic || !out || !tin || !tout || n < 0) return IA_ERR_INVALID_ARG;
+    if (n == 0) return IA_OK;
+    if (!ic->y0 || !ic->phi0 || ic->ld < n) return IA_ERR_INVALID_ARG;
+    if (!out->theta_s || !out->dp || !out->dE_ion || !out->t_final || !out->t_first_bounce ||
+        !out->t_last_bounce || !out->n_bounce || !out->status || !out->n_steps || !out->n_rej)
+        return IA_ERR_INVALID_ARG;
+    if (out->y_final && out->ld < n) return IA_ERR_INVALID_ARG;
+    if (tin->ndir < 1 || tin->ndir > 4 || !tin->dy0 || tin->ld < n) return IA_ERR_INVALID_ARG;
+    if (!tout->d_theta_s || !tout->d_dp || !tout->d_dE_ion || !tout->d_t_final || tout->ld < n)
+        return IA_ERR_INVALID_ARG;
+    if (!aligned8(tin->dy0) || !aligned8(tout->d_theta_s) || !aligned8(tout->d_dp) || !aligned8(tout->d_dE_ion) ||
+        !aligned8(tout->d_t_final) || (tout->dy_final && !aligned8(tout->dy_final)) ||
+        (tout->ftle && !aligned8(tout->ftle)))
+        return IA_ERR_ALIGNMENT;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // a 64-bit work counter in the system's scratch
+    int rc = ia_reserve(sys, 0, nullptr);
+    if (rc != IA_OK) return rc;
+    unsigned long long* work = reinterpret_cast<unsigned long long*>(sys->d_scratch);
+    if (cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return IA_ERR_CUDA;
+    IcPtrs icp{ic->y0, ic->phi0, ic->sys_id, nullptr, (long long)ic->ld};
+    ObsPtrs op{out->theta_s, out->dp, out->dE_ion, out->t_final, out->t_first_bounce, out->t_last_bounce,
+               out->n_bounce, out->status, out->n_steps, out->n_rej, out->y_final,
+               (long long)(out->y_final ? out->ld : 0)};
+    TanIn ti;
+    ti.dy0 = tin->dy0;
+    for (int k = 0; k < 4; ++k)
+        for (int j = 0; j < 3; ++j) ti.dq[k][j] = tin->dq[k][j];
+    ti.ndir = tin->ndir;
+    ti.ld = (long long)tin->ld;
+    TanOut to{tout->d_theta_s, tout->d_dp, tout->d_dE_ion, tout->d_t_final, tout->dy_final, tout->ftle,
+              (long long)tout->ld};
+    int resident = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_tangent, 128, 0) != cudaSuccess || resident <= 0)
+        return IA_ERR_CUDA;
+    long long warps = (n + 0);
+    long long grid = (long long)resident * sys->num_sms;
+    if (grid * 4 > warps) grid = (warps + 3) / 4;
+    k_tangent<<<(unsigned)grid, 128, 0, st>>>(sys->d_tab, sys->n_sys, icp, op, (long long)n, ti, to, work);
+    return cudaGetLastError() == cudaSuccess ? IA_OK : IA_ERR_CUDA;
 }
 
 int ia_rcp_check(const double* x, double* y, int64_t n, void* stream)

@@ -54,6 +54,10 @@ struct SysDev {
     double thr_pos, thr_vel;  // atol / rtol, used by the initial-step rule
     double hinit_den;         // 0.8 rtol^(1/5)
     long long max_attempts;
+    // derivatives and scales used by the tangent kernel
+    double kq_per_q;          // d kq_j / d q_j = -(Omega^2/4) 2 s
+    double uq_per_q;          // d uq_j / d q_j = (m_i Omega^2 / 8) 2 s
+    double inv_len, inv_vel;  // 1/r_e and 1/sqrt(2 D_e / mu): units of the FTLE norm
 };
 
 // Output pointers (device, SoA).
@@ -335,6 +339,7 @@ enum LaneResult : int { RUNNING = 0, FINISHED = 1 };
 struct Final {
     double xi[3], vi[3], xa[3], va[3];
     double t;
+    double s_exit;  // fraction of the last step at the r0 crossing (set by finish_exit; -1 otherwise)
     uint32_t status;
 };
 
@@ -573,6 +578,7 @@ __device__ __noinline__ void finish_exit(const SysDev& P, const StepData& D, dou
             fin.va[j] = fma(h, ua, D.va[j]);
         }
         fin.t = t + s * h;
+        fin.s_exit = s;
         fin.status = ST_EXIT;
     } else {
 #pragma unroll
@@ -580,6 +586,7 @@ __device__ __noinline__ void finish_exit(const SysDev& P, const StepData& D, dou
             fin.xi[j] = D.xni[j]; fin.vi[j] = D.vni[j]; fin.xa[j] = D.xna[j]; fin.va[j] = D.vna[j];
         }
         fin.t = t + h;
+        fin.s_exit = -1.0;
         fin.status = ST_EXIT_OUTSIDE;
     }
 }

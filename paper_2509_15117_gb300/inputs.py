@@ -161,6 +161,29 @@ def head_on(theta, phi, r0: float, v0: float) -> np.ndarray:
     return y
 
 
+def head_on_seeds(theta, phi, r0: float, v0: float, E: float) -> np.ndarray:
+    """Derivatives of the head-on initial state with respect to (theta, phi, E): shape (n, 3, 12).
+    x_a = r0 u(theta, phi), v_a = -v0 u with v0 = sqrt(2E/m), so dv0/dE = v0/(2E); E in hartree."""
+    theta = np.asarray(theta, dtype=np.float64)
+    phi = np.asarray(phi, dtype=np.float64)
+    n = theta.shape[0]
+    u = np.stack([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)], axis=1)
+    ut = np.stack([np.cos(theta) * np.cos(phi), np.cos(theta) * np.sin(phi), -np.sin(theta)], axis=1)
+    up = np.stack([-np.sin(theta) * np.sin(phi), np.sin(theta) * np.cos(phi), np.zeros(n)], axis=1)
+    d = np.zeros((n, 3, 12))
+    d[:, 0, 6:9] = r0 * ut
+    d[:, 0, 9:12] = -v0 * ut
+    d[:, 1, 6:9] = r0 * up
+    d[:, 1, 9:12] = -v0 * up
+    d[:, 2, 9:12] = -(v0 / (2.0 * E)) * u
+    return d
+
+
+def q_direction():
+    """d q_vector / d q of the linear trap q = (q, -q, 0)."""
+    return np.array([1.0, -1.0, 0.0])
+
+
 def random_phase(n: int, seed: int) -> np.ndarray:
     """rf phase Omega t0 mod 2 pi, uniform on [0, 2 pi)."""
     return np.random.default_rng(seed).random(n) * (2.0 * math.pi)
