@@ -303,6 +303,63 @@ typedef struct ia_tangent_out {
 int ia_launch_tangent(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* out,
                       const ia_tangent_in* tin, const ia_tangent_out* tout, void* stream);
 
+/* ---- adjoint (reverse-mode) differentiation ---- */
+
+/* Options of ia_launch_adjoint; zero-initialised means defaults. */
+typedef struct ia_adjoint_opts {
+    int32_t seg;            /* committed steps between checkpoints, and the length of a recomputed block;
+                               16..1000000; 0 = 10000 */
+    int32_t max_ckpt;       /* checkpoints kept per trajectory, even, 2..1048576; 0 = 64. A trajectory
+                               longer than seg x max_ckpt steps drops every other checkpoint and doubles
+                               the spacing (memory fixed, recomputation grows) */
+    int64_t warps;          /* trajectories in flight, one warp each; 0 = resident warps; capped at n */
+    void* scratch;          /* device scratch (256-byte aligned) of at least ia_adjoint_scratch_bytes, or
+                               NULL to use the system's own, grown by the launch when needed */
+    int64_t scratch_bytes;  /* size of `scratch` */
+} ia_adjoint_opts;
+
+/* Adjoint results (device pointers). Objectives J_m: m = 0 theta_s, 1 |p_f - p_i|, 2 dE_ion, 3 t_final. */
+typedef struct ia_adjoint_out {
+    double* grad_y0;        /* 4 x 12 x ld: d J_m / d y0[c] of trajectory i at [(m*12 + c)*ld + i], or NULL */
+    double* grad_q;         /* 4 x 3 x ld: d J_m / d q_j at [(m*3 + j)*ld + i], or NULL */
+    double* d_theta_s;      /* ndir x ld: the gradients projected on the seeds (as ia_tangent_out);   */
+    double* d_dp;           /*   required when seeds are given, ignored otherwise                     */
+    double* d_dE_ion;
+    double* d_t_final;
+    int64_t ld;             /* >= n */
+} ia_adjoint_out;
+
+/*
+ * Device scratch an adjoint launch of n trajectories needs: 256 bytes of counters, then per warp in
+ * flight max_ckpt checkpoints of 256 bytes and a step buffer of seg x 128 bytes. sys may be NULL when
+ * opts->warps > 0. Returns the size or a negative code.
+ */
+int64_t ia_adjoint_scratch_bytes(const ia_system* sys, int64_t n, const ia_adjoint_opts* opts);
+
+/*
+ * Integrate n trajectories (as ia_launch, same primal observables bit for bit) and compute, by a
+ * reverse sweep, the gradients of theta_s, |p_f - p_i|, dE_ion and t_final with respect to the initial
+ * state and the trap's q vector. The map differentiated is the one ia_launch_tangent differentiates
+ * (step sizes and decisions held fixed; exit-time sensitivity from the continuous extension), so
+ * for any direction p, grad . (dy0/dp, dq/dp) equals the tangent's derivative up to rounding. The
+ * paper has no counterpart: it studies the sensitivity of these observables to the initial
+ * conditions through fractal maps; the gradients give that sensitivity per trajectory.
+ * Method: the forward pass keeps checkpoints of the complete controller state every opts->seg
+ * committed steps; the reverse pass restores the checkpoint below each block of seg steps, replays
+ * the primal (same decisions) to record the block, and pulls the adjoint back through each DP5 step.
+ * Cost: about four primal integrations (forward, replay, adjoint stages).
+ * seeds (may be NULL): up to 4 directions (ia_tangent_in) whose projections are written to
+ * d_theta_s .. d_t_final. At least one of grad_y0, grad_q or seeds is required.
+ * A trajectory whose replay does not reproduce its forward pass (not expected: the arithmetic is
+ * deterministic) gets NaN derivatives; one with a bad initial state or sys_id gets zeros.
+ * Scratch: opts->scratch, else the system's own (cudaMalloc when it must grow: synchronous).
+ * One warp per trajectory. Asynchronous on `stream`; launches sharing the system's own adjoint
+ * scratch must not overlap.
+ */
+int ia_launch_adjoint(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* out,
+                      const ia_tangent_in* seeds, const ia_adjoint_out* aout, const ia_adjoint_opts* opts,
+                      void* stream);
+
 /*
  * Test hook (no counterpart in the paper): y[i] = 1/x[i] computed as the integrator computes 1/r^2
  * (Newton-Raphson from an FP32 seed). x, y: device arrays of n doubles, x[i] > 0. Asynchronous.

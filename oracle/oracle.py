@@ -290,3 +290,18 @@ def fd_extended(desc: dict, y0, phi0: float, hs, mode: int, dy0, dq, delta: floa
     L.orc_fd_ld(ctypes.byref(s), _dptr(y), phi0, _dptr(hs), len(hs), mode, _dptr(d1), _dptr(d2), delta,
                 _dptr(out))
     return out
+
+
+def gradient(desc: dict, y0, phi0: float, hs, mode: int):
+    """Gradient of (theta_s, dp, dE_ion, t_final) with respect to the initial state and the q vector,
+    along the frozen step sequence: the transpose of the Jacobian, assembled column by column from the
+    discrete tangent along the fifteen unit directions (twelve state components, three q components).
+    Returns (g_y0 (4, 12), g_q (4, 3))."""
+    dirs_y = np.vstack([np.eye(12), np.zeros((3, 12))])
+    dirs_q = np.vstack([np.zeros((12, 3)), np.eye(3)])
+    cols = []
+    for k in range(0, 15, 4):
+        out, _ = tangent(desc, y0, phi0, hs, mode, dirs_y[k:k + 4], dirs_q[k:k + 4])
+        cols.append(out)
+    J = np.vstack(cols)  # (15, 4): row = direction, column = objective
+    return np.ascontiguousarray(J[:12].T), np.ascontiguousarray(J[12:].T)

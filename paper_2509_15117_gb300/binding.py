@@ -31,7 +31,8 @@ ST_COMPLEX = 1 << 8
 
 EXPORTED = ("ia_system_create", "ia_system_destroy", "ia_system_count", "ia_scratch_bytes", "ia_reserve",
             "ia_launch", "ia_launch_static", "ia_reduce_stats", "ia_reserve_stats", "ia_graph_create",
-            "ia_graph_launch", "ia_graph_destroy", "ia_autotune", "ia_launch_tangent", "ia_fp64_peak", "ia_rcp_check",
+            "ia_graph_launch", "ia_graph_destroy", "ia_autotune", "ia_launch_tangent", "ia_adjoint_scratch_bytes", "ia_launch_adjoint",
+            "ia_fp64_peak", "ia_rcp_check",
             "ia_error_string", "ia_version")
 
 STATS_BOUNCE_BINS = 32
@@ -89,6 +90,17 @@ class ia_tangent_in(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("ld", ctypes.c_int64)]
 
 
+class ia_adjoint_opts(ctypes.Structure):
+    _fields_ = [("seg", ctypes.c_int32), ("max_ckpt", ctypes.c_int32), ("warps", ctypes.c_int64),
+                ("scratch", ctypes.c_void_p), ("scratch_bytes", ctypes.c_int64)]
+
+
+class ia_adjoint_out(ctypes.Structure):
+    _fields_ = [("grad_y0", ctypes.c_void_p), ("grad_q", ctypes.c_void_p), ("d_theta_s", ctypes.c_void_p),
+                ("d_dp", ctypes.c_void_p), ("d_dE_ion", ctypes.c_void_p), ("d_t_final", ctypes.c_void_p),
+                ("ld", ctypes.c_int64)]
+
+
 class ia_tangent_out(ctypes.Structure):
     _fields_ = [("d_theta_s", ctypes.c_void_p), ("d_dp", ctypes.c_void_p), ("d_dE_ion", ctypes.c_void_p),
                 ("d_t_final", ctypes.c_void_p), ("dy_final", ctypes.c_void_p), ("ftle", ctypes.c_void_p),
@@ -142,6 +154,11 @@ def load(build_if_missing: bool = True):
     L.ia_launch_tangent.argtypes = [ctypes.c_void_p, P(ia_ic_soa), ctypes.c_int64, P(ia_obs_soa),
                                     P(ia_tangent_in), P(ia_tangent_out), ctypes.c_void_p]
     L.ia_launch_tangent.restype = ctypes.c_int
+    L.ia_adjoint_scratch_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int64, P(ia_adjoint_opts)]
+    L.ia_adjoint_scratch_bytes.restype = ctypes.c_int64
+    L.ia_launch_adjoint.argtypes = [ctypes.c_void_p, P(ia_ic_soa), ctypes.c_int64, P(ia_obs_soa),
+                                    P(ia_tangent_in), P(ia_adjoint_out), P(ia_adjoint_opts), ctypes.c_void_p]
+    L.ia_launch_adjoint.restype = ctypes.c_int
     L.ia_scratch_bytes.argtypes = [ctypes.c_int64, P(ia_launch_opts)]
     L.ia_scratch_bytes.restype = ctypes.c_int64
     L.ia_reserve.argtypes = [ctypes.c_void_p, ctypes.c_int64, P(ia_launch_opts)]
@@ -422,6 +439,73 @@ def ia_launch_tangent(handle: int, y0_soa, phi0, sys_id, out: dict, dy0, dq, tan
     to.ld = n
     _check(load().ia_launch_tangent(handle, ctypes.byref(ic), n, ctypes.byref(o), ctypes.byref(ti), ctypes.byref(to),
                                     _stream_ptr(stream)))
+
+
+OBJECTIVES = ("theta_s", "dp", "dE_ion", "t_final")
+
+
+def make_adjoint_opts(seg: int = 0, max_ckpt: int = 0, warps: int = 0, scratch=None) -> ia_adjoint_opts:
+    o = ia_adjoint_opts()
+    o.seg = int(seg)
+    o.max_ckpt = int(max_ckpt)
+    o.warps = int(warps)
+    if scratch is not None:
+        o.scratch = scratch.data_ptr()
+        o.scratch_bytes = scratch.numel() * scratch.element_size()
+    return o
+
+
+def ia_adjoint_scratch_bytes(handle, n: int, **opts) -> int:
+    """Scratch bytes of an adjoint launch (handle may be None when warps > 0)."""
+    o = make_adjoint_opts(**opts)
+    r = load().ia_adjoint_scratch_bytes(handle, int(n), ctypes.byref(o))
+    if r < 0:
+        _check(int(r))
+    return int(r)
+
+
+def alloc_adjoint(n: int, ndir: int = 0, grad_y0: bool = True, grad_q: bool = True, device="cuda") -> dict:
+    import torch
+    a = {}
+    if grad_y0:
+        a["grad_y0"] = torch.empty((4, 12, n), dtype=torch.float64, device=device)
+    if grad_q:
+        a["grad_q"] = torch.empty((4, 3, n), dtype=torch.float64, device=device)
+    for k in ("d_theta_s", "d_dp", "d_dE_ion", "d_t_final"):
+        if ndir > 0:
+            a[k] = torch.empty((ndir, n), dtype=torch.float64, device=device)
+    return a
+
+
+def ia_launch_adjoint(handle: int, y0_soa, phi0, sys_id, out: dict, adj: dict, dy0=None, dq=None, stream=None,
+                      **opts) -> None:
+    """Adjoint launch: gradients of (theta_s, dp, dE_ion, t_final) w.r.t. y0 and q into adj["grad_y0"]
+    (4, 12, n) and adj["grad_q"] (4, 3, n); with seeds dy0 (ndir, 12, n) device and dq (ndir, 3) host,
+    their projections into adj["d_theta_s"] .. adj["d_t_final"] (ndir, n). opts: seg, max_ckpt, warps,
+    scratch (a device tensor)."""
+    n = int(phi0.shape[0])
+    ic = _ic_struct(y0_soa, phi0, sys_id, None)
+    o = _obs_struct(out, n)
+    ti = None
+    if dy0 is not None:
+        ti = ia_tangent_in()
+        ndir = int(dy0.shape[0])
+        ti.dy0 = dy0.data_ptr()
+        dqa = np.zeros((4, 3)) if dq is None else np.asarray(dq, dtype=np.float64)
+        for k in range(ndir):
+            for j in range(3):
+                ti.dq[k][j] = float(dqa[k, j])
+        ti.ndir = ndir
+        ti.reserved = 0
+        ti.ld = n
+    ao = ia_adjoint_out()
+    for k in ("grad_y0", "grad_q", "d_theta_s", "d_dp", "d_dE_ion", "d_t_final"):
+        setattr(ao, k, adj[k].data_ptr() if k in adj else None)
+    ao.ld = n
+    op = make_adjoint_opts(**opts)
+    _check(load().ia_launch_adjoint(handle, ctypes.byref(ic), n, ctypes.byref(o),
+                                    ctypes.byref(ti) if ti is not None else None, ctypes.byref(ao),
+                                    ctypes.byref(op), _stream_ptr(stream)))
 
 
 class System:

@@ -26,6 +26,7 @@
 #include "ia_traj.cuh"
 #include "ia_stats.cuh"
 #include "ia_tangent.cuh"
+#include "ia_adjoint.cuh"
 #include "../../include/ionatom.h"
 
 using namespace ia;
@@ -52,23 +53,6 @@ __host__ __device__ constexpr size_t ready_bytes(long long cap) { return ((size_
 constexpr unsigned READY_SPIN_LIMIT = 1u << 22;  // record claimed but not yet published: ~0.3-1 s
 constexpr unsigned IDLE_SPIN_LIMIT = 1u << 27;   // tail worker with nothing to do: minutes
 
-__device__ __forceinline__ void store_bad_sid(const IcPtrs& ic, const ObsPtrs& out, const SysDev* tab, long long i)
-{
-    Final fin;
-    Tally S;
-    S.phi0 = 0.0;
-    S.t_first = S.t_last = 0.0;
-    S.n_acc = S.n_rej = S.n_bounce = 0;
-    const double* y = ic.y0 + i;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        fin.xi[j] = y[(0 + j) * ic.ld]; fin.vi[j] = y[(3 + j) * ic.ld];
-        fin.xa[j] = y[(6 + j) * ic.ld]; fin.va[j] = y[(9 + j) * ic.ld];
-    }
-    fin.t = 0.0;
-    fin.status = ST_BAD_IC;
-    store_result(tab[0], ic, out, i, S, fin, false);
-}
 
 __global__ void __launch_bounds__(128) k_plain(const SysDev* __restrict__ tab, int n_sys, IcPtrs ic,
                                                ObsPtrs out, long long n)
@@ -774,6 +758,8 @@ struct ia_system {
     size_t scratch_bytes;
     void* d_stats_scratch;    // block partials of the statistics reduction
     size_t stats_scratch_bytes;
+    void* d_adj_scratch;      // checkpoints and step buffers of adjoint launches (grown on demand)
+    size_t adj_scratch_bytes;
     int num_sms;
 };
 
@@ -938,6 +924,8 @@ int ia_system_create(const ia_system_desc* desc, int32_t n_sys, ia_system** out)
     s->scratch_bytes = 0;
     s->d_stats_scratch = nullptr;
     s->stats_scratch_bytes = 0;
+    s->d_adj_scratch = nullptr;
+    s->adj_scratch_bytes = 0;
     s->num_sms = prop.multiProcessorCount;
     if (cudaMalloc(&s->d_tab, sizeof(SysDev) * (size_t)n_sys) != cudaSuccess ||
         cudaMemcpy(s->d_tab, host, sizeof(SysDev) * (size_t)n_sys, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -957,6 +945,7 @@ int ia_system_destroy(ia_system* sys)
     cudaFree(sys->d_tab);
     cudaFree(sys->d_scratch);
     cudaFree(sys->d_stats_scratch);
+    cudaFree(sys->d_adj_scratch);
     delete sys;
     return IA_OK;
 }
@@ -1343,6 +1332,133 @@ int ia_launch_tangent(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_o
     long long grid = (long long)resident * sys->num_sms;
     if (grid * 4 > warps) grid = (warps + 3) / 4;
     k_tangent<<<(unsigned)grid, 128, 0, st>>>(sys->d_tab, sys->n_sys, icp, op, (long long)n, ti, to, work);
+    return cudaGetLastError() == cudaSuccess ? IA_OK : IA_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Adjoint launch
+
+namespace {
+
+constexpr int ADJ_DEFAULT_SEG = 10000;
+constexpr int ADJ_DEFAULT_CKPT = 64;
+constexpr size_t ADJ_HEAD = 256;
+
+struct AdjResolved {
+    long long warps;
+    int seg, max_ckpt;
+    size_t bytes;
+};
+
+int adj_resolve(const ia_system* sys, int64_t n, const ia_adjoint_opts* opts, AdjResolved& r)
+{
+    ia_adjoint_opts o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (n < 0 || o.seg < 0 || o.max_ckpt < 0 || o.warps < 0 || o.scratch_bytes < 0) return IA_ERR_INVALID_ARG;
+    r.seg = o.seg ? o.seg : ADJ_DEFAULT_SEG;
+    r.max_ckpt = o.max_ckpt ? o.max_ckpt : ADJ_DEFAULT_CKPT;
+    if (r.seg < 16 || r.seg > 1000000 || r.max_ckpt < 2 || r.max_ckpt > 1048576 || (r.max_ckpt & 1))
+        return IA_ERR_INVALID_ARG;
+    long long w = o.warps;
+    if (w == 0) {
+        if (!sys) return IA_ERR_INVALID_ARG;
+        int resident = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_adjoint, 128, 0) != cudaSuccess ||
+            resident <= 0)
+            return IA_ERR_CUDA;
+        w = (long long)resident * sys->num_sms * ADJ_WARPS;
+    }
+    if (w > n) w = n;
+    if (w < 1) w = 1;
+    if (w > (1ll << 24)) return IA_ERR_TOO_LARGE;
+    r.warps = w;
+    const size_t per = (size_t)r.max_ckpt * CK_DOUBLES * 8u + (size_t)r.seg * SR_DOUBLES * 8u;
+    r.bytes = ADJ_HEAD + (size_t)w * per;
+    return IA_OK;
+}
+
+}  // namespace
+
+int64_t ia_adjoint_scratch_bytes(const ia_system* sys, int64_t n, const ia_adjoint_opts* opts)
+{
+    AdjResolved r;
+    const int rc = adj_resolve(sys, n, opts, r);
+    if (rc != IA_OK) return rc;
+    return (int64_t)r.bytes;
+}
+
+int ia_launch_adjoint(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* out,
+                      const ia_tangent_in* seeds, const ia_adjoint_out* aout, const ia_adjoint_opts* opts,
+                      void* stream)
+{
+    if (!sys || !ic || !out || !aout || n < 0) return IA_ERR_INVALID_ARG;
+    if (n == 0) return IA_OK;
+    if (!ic->y0 || !ic->phi0 || ic->ld < n) return IA_ERR_INVALID_ARG;
+    if (!out->theta_s || !out->dp || !out->dE_ion || !out->t_final || !out->t_first_bounce ||
+        !out->t_last_bounce || !out->n_bounce || !out->status || !out->n_steps || !out->n_rej)
+        return IA_ERR_INVALID_ARG;
+    if (out->y_final && out->ld < n) return IA_ERR_INVALID_ARG;
+    if (!aligned8(ic->y0) || !aligned8(ic->phi0) || !aligned8(out->theta_s) || !aligned8(out->dp) ||
+        !aligned8(out->dE_ion) || !aligned8(out->t_final) || !aligned8(out->t_first_bounce) ||
+        !aligned8(out->t_last_bounce) || (out->y_final && !aligned8(out->y_final)))
+        return IA_ERR_ALIGNMENT;
+    const int ndir = seeds ? seeds->ndir : 0;
+    if (seeds && (ndir < 1 || ndir > 4 || !seeds->dy0 || seeds->ld < n || seeds->reserved != 0))
+        return IA_ERR_INVALID_ARG;
+    if (!aout->grad_y0 && !aout->grad_q && ndir == 0) return IA_ERR_INVALID_ARG;
+    if ((aout->grad_y0 || aout->grad_q || ndir > 0) && aout->ld < n) return IA_ERR_INVALID_ARG;
+    if (ndir > 0 && (!aout->d_theta_s || !aout->d_dp || !aout->d_dE_ion || !aout->d_t_final))
+        return IA_ERR_INVALID_ARG;
+    if ((aout->grad_y0 && !aligned8(aout->grad_y0)) || (aout->grad_q && !aligned8(aout->grad_q)) ||
+        (ndir > 0 && (!aligned8(seeds->dy0) || !aligned8(aout->d_theta_s) || !aligned8(aout->d_dp) ||
+                      !aligned8(aout->d_dE_ion) || !aligned8(aout->d_t_final))))
+        return IA_ERR_ALIGNMENT;
+    AdjResolved r;
+    int rc = adj_resolve(sys, n, opts, r);
+    if (rc != IA_OK) return rc;
+    void* scratch = opts ? opts->scratch : nullptr;
+    if (scratch) {
+        if ((reinterpret_cast<uintptr_t>(scratch) & 255u) != 0) return IA_ERR_ALIGNMENT;
+        if ((size_t)opts->scratch_bytes < r.bytes) return IA_ERR_INVALID_ARG;
+    } else {
+        if (r.bytes > sys->adj_scratch_bytes) {
+            void* p = nullptr;
+            if (cudaMalloc(&p, r.bytes) != cudaSuccess) return IA_ERR_CUDA;
+            cudaFree(sys->d_adj_scratch);
+            sys->d_adj_scratch = p;
+            sys->adj_scratch_bytes = r.bytes;
+        }
+        scratch = sys->d_adj_scratch;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char* base = static_cast<unsigned char*>(scratch);
+    if (cudaMemsetAsync(base, 0, ADJ_HEAD, st) != cudaSuccess) return IA_ERR_CUDA;
+    AdjBuf buf;
+    buf.work = reinterpret_cast<unsigned long long*>(base);
+    buf.errors = reinterpret_cast<unsigned long long*>(base + 8);
+    buf.ckpt = reinterpret_cast<double*>(base + ADJ_HEAD);
+    buf.steps = buf.ckpt + (size_t)r.warps * r.max_ckpt * CK_DOUBLES;
+    buf.warps = r.warps;
+    buf.max_ckpt = r.max_ckpt;
+    buf.seg = r.seg;
+    IcPtrs icp{ic->y0, ic->phi0, ic->sys_id, nullptr, (long long)ic->ld};
+    ObsPtrs op{out->theta_s, out->dp, out->dE_ion, out->t_final, out->t_first_bounce, out->t_last_bounce,
+               out->n_bounce, out->status, out->n_steps, out->n_rej, out->y_final,
+               (long long)(out->y_final ? out->ld : 0)};
+    AdjIn ai;
+    std::memset(&ai, 0, sizeof(ai));
+    ai.ndir = ndir;
+    if (ndir > 0) {
+        ai.dy0 = seeds->dy0;
+        for (int k = 0; k < 4; ++k)
+            for (int j = 0; j < 3; ++j) ai.dq[k][j] = seeds->dq[k][j];
+        ai.ld = (long long)seeds->ld;
+    }
+    AdjOut ao{aout->grad_y0, aout->grad_q, aout->d_theta_s, aout->d_dp, aout->d_dE_ion, aout->d_t_final,
+              (long long)aout->ld};
+    const long long grid = (r.warps + ADJ_WARPS - 1) / ADJ_WARPS;
+    k_adjoint<<<(unsigned)grid, 128, 0, st>>>(sys->d_tab, sys->n_sys, icp, op, (long long)n, ai, ao, buf);
     return cudaGetLastError() == cudaSuccess ? IA_OK : IA_ERR_CUDA;
 }
 

@@ -878,4 +878,23 @@ __device__ __forceinline__ double accel_group(const SysDev& P, const GroupLane<G
     return fma(kc, p, q);
 }
 
+// Result of a trajectory whose sys_id is outside the table: its initial state, BAD_IC.
+__device__ __forceinline__ void store_bad_sid(const IcPtrs& ic, const ObsPtrs& out, const SysDev* tab, long long i)
+{
+    Final fin;
+    Tally S;
+    S.phi0 = 0.0;
+    S.t_first = S.t_last = 0.0;
+    S.n_acc = S.n_rej = S.n_bounce = 0;
+    const double* y = ic.y0 + i;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        fin.xi[j] = y[(0 + j) * ic.ld]; fin.vi[j] = y[(3 + j) * ic.ld];
+        fin.xa[j] = y[(6 + j) * ic.ld]; fin.va[j] = y[(9 + j) * ic.ld];
+    }
+    fin.t = 0.0;
+    fin.status = ST_BAD_IC;
+    store_result(tab[0], ic, out, i, S, fin, false);
+}
+
 }  // namespace ia

@@ -94,3 +94,17 @@ def test_stats_layout_and_host_statistics():
     assert s["mean_dE_ion"] == pytest.approx(0.002)
     assert s["survival"][0] == 1.0 and s["survival"][11] == pytest.approx(130 / 430)
     assert s["survival"][21] == 0.0
+
+
+def test_adjoint_structs_and_scratch_arithmetic_without_gpu():
+    assert ctypes.sizeof(Bd.ia_adjoint_opts) == 4 * 2 + 8 * 3
+    assert ctypes.sizeof(Bd.ia_adjoint_out) == 8 * 7
+    # 256 B of counters + per warp: max_ckpt checkpoints of 256 B and seg step records of 128 B
+    assert Bd.ia_adjoint_scratch_bytes(None, 1000, warps=10) == 256 + 10 * (64 * 256 + 10000 * 128)
+    assert Bd.ia_adjoint_scratch_bytes(None, 3, warps=10, seg=16, max_ckpt=4) == 256 + 3 * (4 * 256 + 16 * 128)
+    for bad in (dict(warps=4, max_ckpt=3), dict(warps=4, seg=8), dict(warps=4, max_ckpt=-2), dict(warps=-1)):
+        with pytest.raises(Bd.IaError):
+            Bd.ia_adjoint_scratch_bytes(None, 10, **bad)
+    # default warps need the device's occupancy, hence a system
+    with pytest.raises(Bd.IaError):
+        Bd.ia_adjoint_scratch_bytes(None, 10)
