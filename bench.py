@@ -34,9 +34,12 @@ METRIC = "trajectories/s and RHS evals/s at rtol 1e-10 FP64, plain vs batched/ad
 UNIT = "trajectories/s"
 GRID = 1024
 
-# FP64 floating-point operations per attempted DP5 step of the kernel (fused multiply-add = 2),
-# counted by ncu's per-thread FP64 instruction counters (2 dfma + dmul + dadd, predicated-on threads)
-# on the persistent kernel, divided by the attempted steps of that launch. See profiles/.
+# FP64 floating-point operations per attempted DP5 step of the one-lane-per-trajectory arithmetic
+# (fused multiply-add = 2), counted by ncu's per-thread FP64 instruction counters (2 dfma + dmul + dadd,
+# predicated-on threads) on the plain kernel, divided by the attempted steps of that launch; the cos
+# and reciprocal instruction sequences are included. The persistent kernel runs the same arithmetic per
+# attempt in its lane phase (its tail phase spreads one trajectory over six lanes and executes more
+# FP64 instructions in total), so this is the useful work per attempt.
 FLOPS_PER_ATTEMPT = 902.0
 
 
@@ -60,6 +63,9 @@ def parse():
     p.add_argument("--tail-group", type=int, default=0)
     p.add_argument("--tail-blocks-per-sm", type=int, default=0)
     p.add_argument("--tail-sms", type=int, default=0)
+    p.add_argument("--diff-sample", type=int, default=4096,
+                   help="trajectories of the differentiation workload timed through the tangent and adjoint "
+                        "kernels (0: skip)")
     p.add_argument("--profile-case", action="store_true",
                    help="run the persistent and plain kernels once on a small batch (for ncu) and exit")
     return p.parse_args()
@@ -84,6 +90,57 @@ def profile_case():
     torch.cuda.synchronize()
     n = int(out["n_steps"].sum().item() + out["n_rej"].sum().item())
     print(json.dumps({"profile_case": "Rb 1 mK head-on 64x64", "trajectories": len(y0), "attempted_steps": n}))
+
+
+def diff_bench(n: int, flush):
+    """Tangent (4 seeds + FTLE) and adjoint (4 objectives, projected on the same seeds) launches on the
+    first n trajectories of the differentiation workload (Yb+-Rb head-on, 1.5 uK, (theta, phi) uniform
+    on the octant, seed 5), each timed with CUDA events after a warm-up launch on 64 of them, next to
+    the persistent primal launch on the same trajectories."""
+    import torch
+    from paper_2509_15117_gb300 import binding as Bd
+    sysd, y0, phi0, seeds, dq = I.c5_workload(n)
+    dy0 = np.concatenate([seeds, np.zeros((n, 1, 12))], axis=1)
+    stream = torch.cuda.current_stream()
+    res = {}
+    with Bd.System([sysd.as_dict()]) as S:
+        def run(kind, m):
+            y, p, _ = Bd.to_device_soa(y0[:m], phi0[:m], None)
+            dyd = torch.from_numpy(np.ascontiguousarray(np.transpose(dy0[:m], (1, 2, 0)))).cuda()
+            out = Bd.alloc_obs(m)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if kind == "tangent":
+                tan = Bd.alloc_tangent(m, 4)
+                flush.zero_()
+                e0.record(stream)
+                Bd.ia_launch_tangent(S.handle, y, p, None, out, dyd, dq, tan)
+            elif kind == "adjoint":
+                adj = Bd.alloc_adjoint(m, 4)
+                flush.zero_()
+                e0.record(stream)
+                Bd.ia_launch_adjoint(S.handle, y, p, None, out, adj, dyd, dq)
+            else:
+                flush.zero_()
+                e0.record(stream)
+                Bd.ia_launch(S.handle, y, p, None, out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            att = int((out["n_steps"].to(torch.int64) + out["n_rej"].to(torch.int64)).sum().item())
+            return e0.elapsed_time(e1), att
+        for kind in ("primal", "tangent", "adjoint"):
+            run(kind, 64)
+            ms, att = run(kind, n)
+            res[kind] = (ms, att)
+    wl = ("Yb+-Rb head-on, E = 1.5 uK, D_e = 1 K, q = 0.1, t_max = 1 ms, (theta, phi) uniform on the "
+          f"octant (seed 5), first {n} trajectories")
+    base = {"unit": UNIT, "trajectories": n, "workload": wl,
+            "attempted_steps_per_trajectory": res["primal"][1] / n,
+            "primal_persistent_ms_same_sample": res["primal"][0]}
+    tan = dict(base, value=n / (res["tangent"][0] / 1e3), ms=res["tangent"][0], directions=4, ftle=True,
+               cost_vs_primal=res["tangent"][0] / res["primal"][0])
+    adj = dict(base, value=n / (res["adjoint"][0] / 1e3), ms=res["adjoint"][0], objectives=4, seeds=4,
+               checkpoint_every=10000, cost_vs_primal=res["adjoint"][0] / res["primal"][0])
+    return tan, adj
 
 
 def dist_env():
@@ -155,47 +212,62 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(seconds: float):
-    """The oracle, as it stands, on all host cores, over a bounded sample of the same workload:
-    trajectories drawn evenly from the first step's batch until about `seconds` of CPU work."""
+def _oracle_sample(seconds: float, steps: int = 1, warmup: int = 0):
+    """The oracle, as it stands, on all host cores, over bounded samples of the same workload:
+    trajectories drawn uniformly at random (seed 12345) from the step-0 batch at grid stride 4, in
+    chunks, until each of `steps` timed steps has used about seconds/steps of wall time; `warmup`
+    small untimed chunks first."""
     from oracle import oracle as O
     systems, y0, phi0, sid = batch(0, 4)
     descs = [s.as_dict() for s in systems]
     n_all = len(y0)
     cores = O.max_threads()
-    rng = np.random.default_rng(12345)
-    order = rng.permutation(n_all)
-    done = 0
-    t_used = 0.0
-    steps = 0
-    chunk = max(cores * 4, 64)
-    while t_used < seconds and done < n_all:
-        idx = np.sort(order[done:done + chunk])
-        t0 = time.perf_counter()
-        r = O.run_batch(descs, y0[idx], phi0[idx], sid[idx], nthreads=cores)
-        t_used += time.perf_counter() - t0
-        steps += int(np.sum(r["n_steps"] + r["n_rej"]))
-        done += len(idx)
-        chunk = min(chunk * 2, 4096)
-    rate = done / t_used
-    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "rhs_evals_per_s": (6 * steps + done) / t_used,
+    order = np.random.default_rng(12345).permutation(n_all)
+    pos = 0
+    for _ in range(warmup):
+        idx = np.sort(order[pos:pos + 2 * cores])
+        pos += len(idx)
+        O.run_batch(descs, y0[idx], phi0[idx], sid[idx], nthreads=cores)
+    per_step = seconds / max(steps, 1)
+    done = attempts = 0
+    step_s = []
+    for _ in range(steps):
+        t_step = 0.0
+        chunk = max(cores * 4, 64)
+        while t_step < per_step and pos < n_all:
+            idx = np.sort(order[pos:pos + chunk])
+            pos += len(idx)
+            t0 = time.perf_counter()
+            r = O.run_batch(descs, y0[idx], phi0[idx], sid[idx], nthreads=cores)
+            t_step += time.perf_counter() - t0
+            attempts += int(np.sum(r["n_steps"] + r["n_rej"]))
+            done += len(idx)
+            chunk = min(chunk * 2, 4096)
+        step_s.append(t_step)
+    t_used = float(sum(step_s))
+    return {"value": done / t_used, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "rhs_evals_per_s": (6 * attempts + done) / t_used, "ms_per_step": 1e3 * t_used / max(steps, 1),
             "sample": f"{done} trajectories drawn uniformly at random (seed 12345) from the step-0 batch "
                       f"(species x energy sweep, grid stride 4), {t_used:.1f} s on {cores} threads"}
 
 
+def cpu_baseline(seconds: float):
+    return _oracle_sample(seconds)
+
+
 def run_reference(args, rank, world):
+    """The reference arm: the oracle timed on the host cores (rank 0 only)."""
     if rank != 0:
         return
-    cb = cpu_baseline(max(args.cpu_seconds, 5.0) / max(args.steps, 1) * max(args.steps, 1))
+    cb = _oracle_sample(max(args.cpu_seconds, 5.0), steps=args.steps, warmup=args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "Yb+ head-on species x energy sweep (5 species x 8 energies, 1024^2 "
                                "octant grid, D_e = 1 K, q = 0.1, t_max = 1 ms), bounded sample",
                    "rtol": 1e-10},
-        "cpu_baseline": cb,
+        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "rhs_evals_per_s": cb["rhs_evals_per_s"],
     }
@@ -347,6 +419,10 @@ def main():
         e2e = {"value": n * world / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    diff = None
+    if rank == 0 and args.diff_sample > 0:
+        diff = diff_bench(args.diff_sample, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -381,6 +457,8 @@ def main():
             "clocks": clk,
             "wall_s": wall,
         }
+        if diff is not None:
+            line["tangent"], line["adjoint"] = diff
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

@@ -359,3 +359,31 @@ def c4_workload(scale: float = 1.0, seed: int = 4, t_max_s: float = 1e-3):
         sids.append(np.full(n, k, dtype=np.int32))
         systems.append(sysd)
     return systems, np.concatenate(ys), np.concatenate(ps), np.concatenate(sids)
+
+
+def c5_workload(n: int = 1_000_000, seed: int = 5, t_max_s: float = 1e-3):
+    """Differentiation workload: Yb+-Rb head-on at E = 1.5 uK (D_e = 1 K, q = 0.1, a = 0, r0 = 5000 a0),
+    (theta, phi) uniform on the octant surface, rf phase 0. Returns (system, y0, phi0, seeds, dq) with
+    seeds (n, 3, 12) = d y0 / d(theta, phi, E) and dq (4, 3): zero for those three, the q direction of
+    the linear trap for the fourth seed (whose d y0 is zero)."""
+    E_K = 1.5e-6
+    sysd = make_system("Rb", De_K=1.0, q=0.1, a=0.0, r0=5000.0, t_max_s=t_max_s, E_K=E_K)
+    th, ph = octant_random(n, seed)
+    v0 = speed_for_energy(kelvin(E_K), sysd.m_atom)
+    y0 = head_on(th, ph, sysd.r0, v0)
+    seeds = head_on_seeds(th, ph, sysd.r0, v0, kelvin(E_K))
+    dq = np.zeros((4, 3))
+    dq[3] = q_direction()
+    return sysd, y0, np.zeros(n), seeds, dq
+
+
+def c5_ftle_grid(n_grid: int = 2048, t_max_s: float = 1e-3):
+    """FTLE map of the differentiation workload: cell-centred n_grid x n_grid (theta, phi) octant grid
+    with the theta seed as the tangent direction. Returns (system, y0, phi0, dy0 (n, 1, 12))."""
+    E_K = 1.5e-6
+    sysd = make_system("Rb", De_K=1.0, q=0.1, a=0.0, r0=5000.0, t_max_s=t_max_s, E_K=E_K)
+    th, ph = octant_grid(n_grid)
+    v0 = speed_for_energy(kelvin(E_K), sysd.m_atom)
+    y0 = head_on(th, ph, sysd.r0, v0)
+    seeds = head_on_seeds(th, ph, sysd.r0, v0, kelvin(E_K))[:, :1, :]
+    return sysd, y0, np.zeros(len(th)), seeds
