@@ -5,8 +5,10 @@ Workload: the head-on species x energy sweep (Yb+ with Li, Na, K, Rb, Cs; 8 ener
 octant grid. One step integrates one batch: every `stride`-th grid point in each direction of all
 40 (species, energy) systems, with the grid offset advanced every step so successive steps see
 different trajectories. Trajectory lengths differ by 10-100x, so the persistent kernel with work-queue
-refill is the timed path; the plain one-thread-per-trajectory kernel is timed on the same batch for
-the speedup.
+refill is the timed path; the plain one-thread-per-trajectory kernel is timed on a subsample of the
+same batch for the speedup. Each timed step copies its inputs from pinned host memory, flushes L2,
+launches (device-timed with CUDA events: `value`) and copies the observables back (the whole step:
+`e2e`).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--stride S]
 Prints one JSON line.
@@ -53,7 +55,6 @@ def parse():
     p.add_argument("--warmup-stride", type=int, default=64)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-plain", action="store_true")
-    p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--block", type=int, default=0)
     p.add_argument("--refill", type=int, default=0)
@@ -68,19 +69,22 @@ def parse():
                         "kernels (0: skip)")
     p.add_argument("--profile-case", action="store_true",
                    help="run the persistent and plain kernels once on a small batch (for ncu) and exit")
+    p.add_argument("--profile-grid", type=int, default=64,
+                   help="(theta, phi) grid points per direction of the profile case")
     return p.parse_args()
 
 
-def profile_case():
-    """Small fixed case for ncu captures: 4096 head-on Rb trajectories at 1 mK on a 64 x 64 octant grid
-    (short, single-bounce dominated), run by the persistent kernel (default budget: its tail kernel
-    gets no work), by the persistent kernel with a 300-step budget (the tail kernel finishes almost
-    every trajectory) and by the plain kernel."""
+def profile_case(n_grid: int = 64):
+    """Small fixed case for ncu captures: head-on Rb trajectories at 1 mK on an n_grid x n_grid octant
+    grid (short, single-bounce dominated; 64 x 64 = 4096 leaves most lanes idle and shows the latency
+    of one wave, 512 x 512 = 262144 fills every lane several times and shows the bulk phase), run by
+    the persistent kernel (default budget: its tail phase gets no work), by the persistent kernel with
+    a 300-step budget (the tail phase finishes almost every trajectory) and by the plain kernel."""
     import torch
     from paper_2509_15117_gb300 import binding as Bd
     systems = I.c2_systems()
     rb_hot = [s for (sp, E, s) in systems if sp == "Rb"][-1]
-    th, ph = I.octant_grid(64)
+    th, ph = I.octant_grid(n_grid)
     v0 = I.speed_for_energy(I.kelvin(I.C2_ENERGIES_K[-1]), rb_hot.m_atom)
     y0 = I.head_on(th, ph, rb_hot.r0, v0)
     with Bd.System([rb_hot.as_dict()]) as S:
@@ -89,7 +93,8 @@ def profile_case():
             out = S.run(y0, np.zeros(len(y0)), None, kernel=kernel, **kw)
     torch.cuda.synchronize()
     n = int(out["n_steps"].sum().item() + out["n_rej"].sum().item())
-    print(json.dumps({"profile_case": "Rb 1 mK head-on 64x64", "trajectories": len(y0), "attempted_steps": n}))
+    print(json.dumps({"profile_case": f"Rb 1 mK head-on {n_grid}x{n_grid}", "trajectories": len(y0),
+                      "attempted_steps": n}))
 
 
 def diff_bench(n: int, flush):
@@ -287,7 +292,7 @@ def main():
     args = parse()
     rank, world, local = dist_env()
     if args.profile_case:
-        profile_case()
+        profile_case(args.profile_grid)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -312,54 +317,74 @@ def main():
           "regs_variant": args.regs_variant, "slice_budget": args.slice_budget, "tail_group": args.tail_group,
           "tail_blocks_per_sm": args.tail_blocks_per_sm, "tail_sms": args.tail_sms}
 
-    # resident inputs for every step (host-side generation is outside the timed region)
-    batches = []
+    # every step's inputs in pinned host memory and its device buffers (generation outside the timing)
+    steps = []
     for s in range(args.steps):
         systems, y0, phi0, sid, order = step_inputs(s, args.stride, rank, world)
-        y, p, d = Bd.to_device_soa(y0, phi0, sid)
-        o = torch.from_numpy(order).cuda()
-        batches.append((y, p, d, o, len(phi0)))
+        n = len(phi0)
+        h = {"y": torch.from_numpy(np.ascontiguousarray(y0.T)).pin_memory(),
+             "p": torch.from_numpy(phi0).pin_memory(), "s": torch.from_numpy(sid).pin_memory(),
+             "o": torch.from_numpy(order).pin_memory()}
+        dv = {k: torch.empty(v.shape, dtype=v.dtype, device="cuda") for k, v in h.items()}
+        out = Bd.alloc_obs(n)
+        hout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+        steps.append({"n": n, "h": h, "d": dv, "out": out, "hout": hout, "order": order})
     descs = [s.as_dict() for s in systems]
     sysh = Bd.System(descs)
-    n_max = max(b[4] for b in batches)
+    n_max = max(st["n"] for st in steps)
     Bd.ia_reserve(sysh.handle, n_max, kernel=Bd.IA_KERNEL_PERSISTENT, slice_budget=args.slice_budget)
-    outs = [Bd.alloc_obs(b[4]) for b in batches]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
 
-    # warm-up steps on small batches of the same workload
+    # warm-up launches of the same kernel on small batches of the workload's short trajectories (the
+    # 1 mK systems of a sparse grid), so that they take seconds, not a long complex's latency
     for w in range(args.warmup):
         systems_w, y0, phi0, sid, order = step_inputs(1000 + w, args.warmup_stride, rank, world)
-        y, p, d = Bd.to_device_soa(y0, phi0, sid)
-        o = Bd.alloc_obs(len(phi0))
-        Bd.ia_launch(sysh.handle, y, p, d, o, order=torch.from_numpy(order).cuda(), **kw)
+        keep = np.nonzero(sid % len(I.C2_ENERGIES_K) == len(I.C2_ENERGIES_K) - 1)[0]
+        y, p, d = Bd.to_device_soa(y0[keep], phi0[keep], sid[keep])
+        o = Bd.alloc_obs(len(keep))
+        Bd.ia_launch(sysh.handle, y, p, d, o, **kw)
     torch.cuda.synchronize()
 
     peak_flops = Bd.ia_fp64_peak(4, 20000)
 
+    # timed steps: host -> device copy of the step's inputs, L2 flush, the launch (device-timed for
+    # `value`), device -> host copy of the observables; the whole is the end-to-end time
     clocks = ClockSampler(local)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     barrier()
     clocks.start()
     t0 = time.perf_counter()
-    for s, (y, p, d, o, n) in enumerate(batches):
-        flush.zero_()
+    for s, st in enumerate(steps):
         ev[s][0].record(stream)
-        Bd.ia_launch(sysh.handle, y, p, d, outs[s], order=o, **kw)
+        for k in st["h"]:
+            st["d"][k].copy_(st["h"][k], non_blocking=True)
+        flush.zero_()
         ev[s][1].record(stream)
+        Bd.ia_launch(sysh.handle, st["d"]["y"], st["d"]["p"], st["d"]["s"], st["out"], order=st["d"]["o"], **kw)
+        ev[s][2].record(stream)
+        for k in st["out"]:
+            st["hout"][k].copy_(st["out"][k], non_blocking=True)
+        ev[s][3].record(stream)
     barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
-    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    lane_ms, dev_ms = Bd.ia_launch_phases(sysh.handle)  # the last step's launch
+    kern_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     total_ms = float(sum(kern_ms))
-    n_local = sum(b[4] for b in batches)
+    n_local = sum(st["n"] for st in steps)
+    outs = [st["out"] for st in steps]
     attempts = sum(int((o["n_steps"].to(torch.int64) + o["n_rej"].to(torch.int64)).sum().item()) for o in outs)
-    max_attempts = max(int((o["n_steps"] + o["n_rej"]).max().item()) for o in outs)
+    per = (outs[0]["n_steps"].to(torch.int64) + outs[0]["n_rej"].to(torch.int64)).cpu().numpy()
+    max_attempts = int(max(int((o["n_steps"] + o["n_rej"]).max().item()) for o in outs))
+    longest = int(np.argmax(per))
+    longest_pos = int(np.nonzero(steps[0]["order"] == longest)[0][0])
     rhs = 6 * attempts + n_local
-    tmax_ms = total_ms
+    tmax_ms, emax_ms = total_ms, float(sum(step_ms))
     if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
+        t = torch.tensor([total_ms, emax_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax_ms = float(t.item())
+        tmax_ms, emax_ms = (float(x) for x in t.tolist())
         c = torch.tensor([float(n_local), float(rhs), float(attempts)], device="cuda", dtype=torch.float64)
         dist.all_reduce(c)
         n_all, rhs_all, att_all = (float(x) for x in c.tolist())
@@ -367,11 +392,17 @@ def main():
         n_all, rhs_all, att_all = float(n_local), float(rhs), float(attempts)
     value = n_all / (tmax_ms / 1e3)
     achieved = FLOPS_PER_ATTEMPT * attempts / (total_ms / 1e3)
+    h2d = sum(v.numel() * v.element_size() for v in steps[0]["h"].values())
+    d2h = sum(v.numel() * v.element_size() for v in steps[0]["hout"].values())
+    e2e = {"value": n_all / (emax_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h), "ms_per_step": emax_ms / args.steps,
+           "path": "ia_launch with the step's inputs copied from pinned host memory and the observables "
+                   "copied back, inside the timed region"}
 
     # plain kernel against the persistent one on a 1/64 subsample of the first step's batch
     plain = None
     if not args.no_plain:
-        y, p, d, o, n = batches[0]
+        y, p, d, n = steps[0]["d"]["y"], steps[0]["d"]["p"], steps[0]["d"]["s"], steps[0]["n"]
         sub = torch.arange(0, n, 64, device="cuda")
         ys, ps, ds = y[:, sub].contiguous(), p[sub].contiguous(), d[sub].contiguous()
         m = int(sub.numel())
@@ -389,35 +420,6 @@ def main():
                  "persistent_ms_same_batch": res["persistent"],
                  "persistent_speedup": res["plain"] / res["persistent"],
                  "batch": "every 64th trajectory of the step-0 batch, same inputs for both kernels"}
-
-    # end to end through the public API: pinned host inputs -> device -> launch -> host outputs
-    e2e = None
-    if not args.no_e2e:
-        systems_e, y0, phi0, sid, order = step_inputs(0, args.stride, rank, world)
-        n = len(phi0)
-        h_y = torch.from_numpy(np.ascontiguousarray(y0.T)).pin_memory()
-        h_p = torch.from_numpy(phi0).pin_memory()
-        h_s = torch.from_numpy(sid).pin_memory()
-        h_o = torch.from_numpy(order).pin_memory()
-        o = Bd.alloc_obs(n)
-        host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in o.items()}
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        y = h_y.to("cuda", non_blocking=True)
-        p = h_p.to("cuda", non_blocking=True)
-        d = h_s.to("cuda", non_blocking=True)
-        oo = h_o.to("cuda", non_blocking=True)
-        Bd.ia_launch(sysh.handle, y, p, d, o, order=oo, **kw)
-        for k in o:
-            host_out[k].copy_(o[k], non_blocking=True)
-        e1.record(stream)
-        barrier()
-        ems = e0.elapsed_time(e1)
-        h2d = h_y.numel() * 8 + h_p.numel() * 8 + h_s.numel() * 4 + h_o.numel() * 8
-        d2h = sum(v.numel() * v.element_size() for v in host_out.values())
-        e2e = {"value": n * world / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
 
     diff = None
     if rank == 0 and args.diff_sample > 0:
@@ -447,6 +449,7 @@ def main():
             "rhs_evals_per_s": rhs_all / (tmax_ms / 1e3),
             "attempted_steps_per_trajectory": att_all / n_all,
             "max_attempted_steps": max_attempts,
+            "longest_trajectory_queue_position": longest_pos / steps[0]["n"],
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_flops / 1e12,
                          "unit": "TFLOP/s", "frac": achieved / peak_flops, "traffic": None,
                          "peak_source": "FP64 FMA microbenchmark (ia_fp64_peak) measured in this run",
@@ -454,6 +457,10 @@ def main():
             "plain": plain,
             "e2e": e2e,
             "gpu_launches": args.steps * (1 if args.slice_budget < 0 else 2),
+            "phases_last_step": {"lane_phase_ms": lane_ms, "kernel_ms": dev_ms,
+                                 "note": "device clock: until the last warp left the lane phase (every "
+                                         "trajectory started; long ones handed to group mode) / until the "
+                                         "last warp finished"},
             "clocks": clk,
             "wall_s": wall,
         }

@@ -195,6 +195,17 @@ int ia_launch_static(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_ob
                      const ia_launch_opts* opts, void* stream);
 
 /*
+ * Phase times of the last persistent launch whose scratch is `scratch` (NULL: the system's own
+ * scratch), from the device clock: *lane_ms = from the first block's start until the last warp left
+ * the lane phase (every trajectory had started and had either finished or been handed to the tail
+ * phase), *total_ms = until the last warp finished. Synchronous (copies 64 bytes from the device; call
+ * it after the launch completed). A diagnostic of how a batch's time splits between the bulk of short
+ * trajectories and the long-lived complexes; no counterpart in the paper. IA_ERR_INVALID_ARG if that
+ * scratch holds no completed persistent launch.
+ */
+int ia_launch_phases(ia_system* sys, const void* scratch, double* lane_ms, double* total_ms);
+
+/*
  * FP64 FMA throughput microbenchmark (no counterpart in the paper: it measures the roofline
  * denominator of the integrator). Runs `blocks_per_sm` x SMs blocks of 256 threads, each thread
  * `iters` iterations of 8 independent fused multiply-add chains, on `stream`, timed with CUDA

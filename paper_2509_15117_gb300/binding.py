@@ -31,9 +31,9 @@ ST_COMPLEX = 1 << 8
 
 EXPORTED = ("ia_system_create", "ia_system_destroy", "ia_system_count", "ia_scratch_bytes", "ia_reserve",
             "ia_launch", "ia_launch_static", "ia_reduce_stats", "ia_reserve_stats", "ia_graph_create",
-            "ia_graph_launch", "ia_graph_destroy", "ia_autotune", "ia_launch_tangent", "ia_adjoint_scratch_bytes", "ia_launch_adjoint",
-            "ia_fp64_peak", "ia_rcp_check",
-            "ia_error_string", "ia_version")
+            "ia_graph_launch", "ia_graph_destroy", "ia_autotune", "ia_launch_phases", "ia_launch_tangent",
+            "ia_adjoint_scratch_bytes", "ia_launch_adjoint", "ia_fp64_peak", "ia_rcp_check", "ia_error_string",
+            "ia_version")
 
 STATS_BOUNCE_BINS = 32
 STATS_LIFETIME_BINS = 64
@@ -154,6 +154,8 @@ def load(build_if_missing: bool = True):
     L.ia_launch_tangent.argtypes = [ctypes.c_void_p, P(ia_ic_soa), ctypes.c_int64, P(ia_obs_soa),
                                     P(ia_tangent_in), P(ia_tangent_out), ctypes.c_void_p]
     L.ia_launch_tangent.restype = ctypes.c_int
+    L.ia_launch_phases.argtypes = [ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_double), P(ctypes.c_double)]
+    L.ia_launch_phases.restype = ctypes.c_int
     L.ia_adjoint_scratch_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int64, P(ia_adjoint_opts)]
     L.ia_adjoint_scratch_bytes.restype = ctypes.c_int64
     L.ia_launch_adjoint.argtypes = [ctypes.c_void_p, P(ia_ic_soa), ctypes.c_int64, P(ia_obs_soa),
@@ -439,6 +441,15 @@ def ia_launch_tangent(handle: int, y0_soa, phi0, sys_id, out: dict, dy0, dq, tan
     to.ld = n
     _check(load().ia_launch_tangent(handle, ctypes.byref(ic), n, ctypes.byref(o), ctypes.byref(ti), ctypes.byref(to),
                                     _stream_ptr(stream)))
+
+
+def ia_launch_phases(handle: int, scratch=None) -> tuple:
+    """(lane-phase ms, total ms) of the last persistent launch on `scratch` (a device tensor) or on
+    the system's own scratch; synchronous."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().ia_launch_phases(handle, scratch.data_ptr() if scratch is not None else None,
+                                   ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 OBJECTIVES = ("theta_s", "dp", "dE_ion", "t_final")

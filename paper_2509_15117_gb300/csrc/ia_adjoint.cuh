@@ -110,7 +110,7 @@ __device__ __forceinline__ void step_coefs(const SysDev& P, int lane, double h, 
 }
 
 // Acceleration component of this lane at positions X of its group (the primal arithmetic of the
-// tangent kernel). When aux is not null, stores the stage quantities the reverse sweep needs.
+// other layouts). When aux is not null, stores the stage quantities the reverse sweep needs.
 __device__ __forceinline__ double adj_accel(const SysDev& P, const TLane& tl, double X, double cs, double kq, double ka,
                                             double coef, double* aux, double& r2, double d[3])
 {
@@ -121,7 +121,8 @@ __device__ __forceinline__ double adj_accel(const SysDev& P, const TLane& tl, do
     const double s = rcp_nr(r2);
     const double s2 = s * s;
     const double s3 = fma(s2, s, 0.0);
-    const double g = s3 * fma(P.c8x8, s2, -P.c4x4);
+    const bool ion = tl.comp < 3;
+    const double gm = s3 * fma(ion ? P.ci8 : P.ca8, s2, -(ion ? P.ci4 : P.ca4));
     d[0] = d0;
     d[1] = d1;
     d[2] = d2;
@@ -130,10 +131,9 @@ __device__ __forceinline__ double adj_accel(const SysDev& P, const TLane& tl, do
         aux[32] = d0;
         aux[64] = d1;
         aux[96] = d2;
-        aux[128] = g;
+        aux[128] = s3 * fma(P.c8x8, s2, -P.c4x4);  // g = -V'(r)/r
         aux[160] = (s2 * s2) * fma(-5.0 * P.c8x8, s2, 3.0 * P.c4x4);
     }
-    const double gm = fma(g, coef, 0.0);
     return fma(fma(kq, cs, ka), X, gm * dd);
 }
 

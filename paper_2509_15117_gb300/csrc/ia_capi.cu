@@ -40,18 +40,28 @@ struct Counters {
     unsigned long long tail;        // next suspend record to resume
     unsigned long long warps_done;  // warps that have left the lane phase
     unsigned long long errors;      // bounded waits that ran out (stays 0 in a healthy run)
-    unsigned long long pad[3];
+    unsigned long long t_start;     // %globaltimer (ns) when the first block started
+    unsigned long long t_lane_end;  // ... when the last warp left the lane phase
+    unsigned long long t_end;       // ... when the last warp finished (fused and clean-up kernels)
     unsigned int sm_claim[192];     // blocks seen per SM, to give one block per reserved SM the tail role
 };
 constexpr size_t SCRATCH_HEAD = 1024;
 static_assert(sizeof(Counters) <= SCRATCH_HEAD, "scratch head");
 constexpr int MAX_TAIL_SMS = 192;
 
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __host__ __device__ constexpr size_t ready_bytes(long long cap) { return ((size_t)cap * 4u + 255u) & ~(size_t)255u; }
 
 // Bounds of the waits in the fused kernel (each wait also sleeps, so these are seconds, not spins).
 constexpr unsigned READY_SPIN_LIMIT = 1u << 22;  // record claimed but not yet published: ~0.3-1 s
 constexpr unsigned IDLE_SPIN_LIMIT = 1u << 27;   // tail worker with nothing to do: minutes
+constexpr unsigned CLAIM_BACKOFF = 64;           // attempts between claim polls of a partly busy warp
 
 
 __global__ void __launch_bounds__(128) k_plain(const SysDev* __restrict__ tab, int n_sys, IcPtrs ic,
@@ -179,9 +189,17 @@ __device__ __forceinline__ void tail_phase(const SysDev* __restrict__ tab, const
     int sid = 0;
     bool active = false, drained = false;
     unsigned idle_spins = 0;
+    unsigned claim_skip = 0;  // iterations without a claim attempt while other groups of the warp run
     for (;;) {
         const bool need = !active && !drained;
-        if (__any_sync(FULL, need)) {
+        bool poll = __any_sync(FULL, need);
+        if (poll && claim_skip > 0 && __any_sync(FULL, active)) {
+            // an idle group polls the record counters (global atomics, microseconds) only every
+            // CLAIM_BACKOFF attempts while its warp still runs other trajectories
+            --claim_skip;
+            poll = false;
+        }
+        if (poll) {
             // the group's first lane claims; the claim is broadcast to the group
             int got = 0;
             unsigned long long k = 0;
@@ -220,6 +238,7 @@ __device__ __forceinline__ void tail_phase(const SysDev* __restrict__ tab, const
             }
             got = __shfl_sync(FULL, got, gl.base);
             k = __shfl_sync(FULL, k, gl.base);
+            if (!__any_sync(FULL, need && got == 1)) claim_skip = CLAIM_BACKOFF;
             if (need) {
                 if (got == 1) {
                     // written by another SM during this launch: read through L2
@@ -280,8 +299,8 @@ __device__ __forceinline__ void tail_phase(const SysDev* __restrict__ tab, const
         const double cs2 = shfl(cl, gl.base + 0), cs3 = shfl(cl, gl.base + 1), cs4 = shfl(cl, gl.base + 2);
         const double cs5 = shfl(cl, gl.base + 3), cs67 = shfl(cl, gl.base + 4);
 
-        const double kq = gl.comp < 3 ? P.kq[gl.comp] : 0.0;
-        const double ka = gl.comp < 3 ? P.ka[gl.comp] : 0.0;
+        const double kq = gl.comp >= 3 ? P.kq[gl.comp - 3] : 0.0;  // lanes 3-5: the ion's axis comp - 3
+        const double ka = gl.comp >= 3 ? P.ka[gl.comp - 3] : 0.0;
         double r2, d3[3];
         const double a2 = accel_group<G>(P, gl, pos2(K, x, v), cs2, kq, ka, r2, d3);
         const double a3 = accel_group<G>(P, gl, pos3(K, x, v, a1), cs3, kq, ka, r2, d3);
@@ -382,6 +401,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sched(const SysDev* __restrict_
 {
     __shared__ int role;  // 0 lane phase first, 1 tail worker, 2 surplus block on a reserved SM
     if (threadIdx.x == 0) {
+        atomicCAS(&ctr->t_start, 0ull, global_ns());
         int r = 0;
         if (budget > 0 && tail_sms > 0) {
             unsigned smid;
@@ -397,10 +417,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sched(const SysDev* __restrict_
     if (r == 0) lane_phase(tab, n_sys, ic, out, n, ctr, ready, susp, cap, refill, budget);
     if ((threadIdx.x & 31) == 0) {
         __threadfence();
-        atomicAdd(&ctr->warps_done, 1ull);
+        if (atomicAdd(&ctr->warps_done, 1ull) + 1ull == total_warps) atomicMax(&ctr->t_lane_end, global_ns());
     }
-    if (r == 2 || budget <= 0) return;
-    tail_phase<G>(tab, ic, out, susp, ready, ctr, cap, wait_ok != 0, total_warps);
+    if (r != 2 && budget > 0) tail_phase<G>(tab, ic, out, susp, ready, ctr, cap, wait_ok != 0, total_warps);
+    if ((threadIdx.x & 31) == 0) atomicMax(&ctr->t_end, global_ns());
 }
 
 // Finishes suspend records left by k_sched (normally none: its workers drain them).
@@ -410,6 +430,7 @@ __global__ void __launch_bounds__(128) k_tail(const SysDev* __restrict__ tab, Ic
                                               Counters* __restrict__ ctr, long long cap)
 {
     tail_phase<G>(tab, ic, out, susp, ready, ctr, cap, false, 0ull);
+    if ((threadIdx.x & 31) == 0) atomicMax(&ctr->t_end, global_ns());
 }
 
 
@@ -798,6 +819,10 @@ SysDev derive(const ia_system_desc& d)
     P.neg_inv_mi = -P.inv_mi;
     P.c8x8 = 8.0 * C8;
     P.c4x4 = 4.0 * C4;
+    P.ci8 = P.c8x8 * P.neg_inv_mi;
+    P.ci4 = P.c4x4 * P.neg_inv_mi;
+    P.ca8 = P.c8x8 * P.inv_ma;
+    P.ca4 = P.c4x4 * P.inv_ma;
     P.Omega = d.Omega;
     const double W2 = d.Omega * d.Omega;
     for (int j = 0; j < 3; ++j) {
@@ -1460,6 +1485,19 @@ int ia_launch_adjoint(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_o
     const long long grid = (r.warps + ADJ_WARPS - 1) / ADJ_WARPS;
     k_adjoint<<<(unsigned)grid, 128, 0, st>>>(sys->d_tab, sys->n_sys, icp, op, (long long)n, ai, ao, buf);
     return cudaGetLastError() == cudaSuccess ? IA_OK : IA_ERR_CUDA;
+}
+
+int ia_launch_phases(ia_system* sys, const void* scratch, double* lane_ms, double* total_ms)
+{
+    if (!sys || !lane_ms || !total_ms) return IA_ERR_INVALID_ARG;
+    const void* base = scratch ? scratch : sys->d_scratch;
+    if (!base) return IA_ERR_INVALID_ARG;
+    Counters c;
+    if (cudaMemcpy(&c, base, sizeof(Counters), cudaMemcpyDeviceToHost) != cudaSuccess) return IA_ERR_CUDA;
+    if (c.t_start == 0 || c.t_end < c.t_start) return IA_ERR_INVALID_ARG;
+    *lane_ms = c.t_lane_end >= c.t_start ? 1e-6 * (double)(c.t_lane_end - c.t_start) : 0.0;
+    *total_ms = 1e-6 * (double)(c.t_end - c.t_start);
+    return IA_OK;
 }
 
 int ia_rcp_check(const double* x, double* y, int64_t n, void* stream)

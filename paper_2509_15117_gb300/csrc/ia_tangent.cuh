@@ -77,14 +77,14 @@ __device__ __forceinline__ double tan_accel(const SysDev& P, const TLane& tl, do
     const double s = rcp_nr(r2);
     const double s2 = s * s;
     const double s3 = fma(s2, s, 0.0);
-    const double f = fma(P.c8x8, s2, -P.c4x4);
-    const double g = s3 * f;
+    // coef g with the 1/m folded into the constants (the primal expression of the other layouts)
+    const bool ion = tl.comp < 3;
+    const double gm = s3 * fma(ion ? P.ci8 : P.ca8, s2, -(ion ? P.ci4 : P.ca4));
     // dg/d(r^2) = s^4 (12 C4 - 40 C8 s^2)
     const double gu = (s2 * s2) * fma(-5.0 * P.c8x8, s2, 3.0 * P.c4x4);
     const double e0 = shfl(dd, tl.base + 0), e1 = shfl(dd, tl.base + 1), e2 = shfl(dd, tl.base + 2);
     const double dot = fma(d0, e0, fma(d1, e1, d2 * e2));
     const double S = tl.dir == 0 ? 0.0 : (2.0 * gu) * dot;
-    const double gm = fma(g, coef, 0.0);
     const double q1 = gm * dd;
     const double dj = j == 0 ? d0 : (j == 1 ? d1 : d2);
     const double q2 = fma(coef * S, dj, q1);

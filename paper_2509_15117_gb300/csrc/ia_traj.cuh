@@ -42,6 +42,8 @@ struct SysDev {
     double inv_mi, inv_ma;  // 1/m
     double neg_inv_mi;      // -1/m_i
     double c8x8, c4x4;      // 8 C8, 4 C4: -V'(r)/r = s^3 (8 C8 s^2 - 4 C4), s = 1/r^2
+    double ci8, ci4;        // -8 C8 / m_i, -4 C4 / m_i: ion acceleration per unit separation = s^3 (ci8 s^2 - ci4)
+    double ca8, ca4;        // 8 C8 / m_a, 4 C4 / m_a: the same for the atom
     double Omega;
     double ka[3];           // ion acceleration per unit displacement, static part: -(Omega^2/4) a_j
     double kq[3];           // rf part, times cos(Omega t + phi0): -(Omega^2/4) 2 s q_j
@@ -164,27 +166,19 @@ __device__ __forceinline__ float rcp_approx_f32(float x)
     return y;
 }
 
-// 1/x for x > 0 by Newton-Raphson on f(y) = 1/y - x (y <- y + y (1 - x y)), seeded by the FP32
-// hardware reciprocal of x truncated to float (seed error < 2^-19); two iterations give ~2^-76
-// before rounding, i.e. within an ulp or two of 1/x. Falls back to division outside the float range.
+// 1/x for x > 0 from the FP32 hardware reciprocal of x truncated to float (seed y0 with relative
+// error < 2^-19), refined by one third-order step of the iteration for 1/x (Householder's method of
+// order 3; equivalently the geometric series 1/x = y0 / (1 - e) = y0 (1 + e + e^2 + ...) truncated
+// after e^2, with e = 1 - x y0): y = y0 + y0 (e + e^2). The truncation error e^3 < 2^-57 is far below
+// the final rounding, so the result is within an ulp of 1/x; three dependent FMAs instead of the four
+// of two Newton steps. Falls back to division outside the float range.
 __device__ __forceinline__ double rcp_nr(double x)
 {
     int e = (__double2hiint(x) >> 20) & 0x7ff;
     if (e < 1023 - 120 || e > 1023 + 120) return 1.0 / x;
-    double y = pos_float_to_double(rcp_approx_f32(nn_to_float(x)));
-    y = fma(y, fma(-x, y, 1.0), y);
-    y = fma(y, fma(-x, y, 1.0), y);
-    return y;
-}
-
-// -V'(r)/r = s^3 (8 C8 s^2 - 4 C4), s = 1/r^2. fma(s2, s, 0) is the rounded product s2*s.
-__device__ __forceinline__ double force_g(const SysDev& P, double r2)
-{
-    double s = rcp_nr(r2);
-    double s2 = s * s;
-    double s3 = fma(s2, s, 0.0);
-    double f = fma(P.c8x8, s2, -P.c4x4);
-    return s3 * f;
+    const double y = pos_float_to_double(rcp_approx_f32(nn_to_float(x)));
+    const double r = fma(-x, y, 1.0);
+    return fma(y, fma(r, r, r), y);
 }
 
 __device__ __forceinline__ double ion_energy(const SysDev& P, double cs, const double xi[3], const double vi[3])
@@ -203,9 +197,12 @@ __device__ __forceinline__ void accel(const SysDev& P, const double xi[3], const
 {
     double d0 = xa[0] - xi[0], d1 = xa[1] - xi[1], d2 = xa[2] - xi[2];
     double r2 = fma(d0, d0, fma(d1, d1, d2 * d2));
-    double g = force_g(P, r2);
-    double gmi = fma(g, P.neg_inv_mi, 0.0);
-    double gma = fma(g, P.inv_ma, 0.0);
+    // -V'(r)/(r m) = s^3 (8 C8 s^2 - 4 C4) / m with s = 1/r^2, the 1/m folded into the constants
+    const double s = rcp_nr(r2);
+    const double s2 = s * s;
+    const double s3 = fma(s2, s, 0.0);
+    const double gmi = s3 * fma(P.ci8, s2, -P.ci4);
+    const double gma = s3 * fma(P.ca8, s2, -P.ca4);
     aa[0] = gma * d0;
     aa[1] = gma * d1;
     aa[2] = gma * d2;
@@ -847,9 +844,10 @@ __device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(F
 
 // Group-mode accelerations: this lane's component of the acceleration at stage positions p (each
 // lane holds its component), cs = cos(Omega t_s + phi0). Same expressions as accel().
+// kq3, ka3: the ion trap coefficients of axis comp - 3 on lanes 3-5 (unused elsewhere).
 template <int G>
 __device__ __forceinline__ double accel_group(const SysDev& P, const GroupLane<G>& gl, double p, double cs,
-                                              double kq, double ka, double& r2out, double d3[3])
+                                              double kq3, double ka3, double& r2out, double d3[3])
 {
     const int j = gl.comp < 3 ? gl.comp : gl.comp - 3;
     const double pi = shfl(p, gl.base + j);
@@ -859,17 +857,16 @@ __device__ __forceinline__ double accel_group(const SysDev& P, const GroupLane<G
     const double r2 = fma(d0, d0, fma(d1, d1, d2 * d2));
     const double s = rcp_nr(r2);
     const double s2 = s * s;
-    // one FMA instruction: lane 0 forms s2*s, lane 1 forms 8 C8 s2 - 4 C4
-    const bool l1 = (gl.c == 1);
-    const double u = fma(l1 ? P.c8x8 : s2, l1 ? s2 : s, l1 ? -P.c4x4 : 0.0);
-    const double g = shfl(u, gl.base + 0) * shfl(u, gl.base + 1);
-    // one FMA instruction: lanes 0-2 form the ion trap coefficients ka + kq cs, lane 3 g*(-1/m_i),
-    // lane 4 g/m_a
-    const bool ion = gl.c < 3;
-    const double mc = gl.c == 3 ? P.neg_inv_mi : P.inv_ma;
-    const double u2 = fma(ion ? kq : g, ion ? cs : mc, ion ? ka : 0.0);
-    const double kc = gl.comp < 3 ? u2 : 0.0;
-    const double gm = shfl(u2, gl.base + (gl.comp < 3 ? 3 : 4));
+    // one FMA instruction: lane 0 forms s2 s, lane 1 the ion's ci8 s2 - ci4, lane 2 the atom's
+    // ca8 s2 - ca4, lanes 3-5 the ion trap coefficients ka_j + kq_j cs (j = lane - 3)
+    const int c = gl.c;
+    const double ua = c == 0 ? s2 : (c == 1 ? P.ci8 : (c == 2 ? P.ca8 : kq3));
+    const double ub = c == 0 ? s : (c < 3 ? s2 : cs);
+    const double uc = c == 0 ? 0.0 : (c == 1 ? -P.ci4 : (c == 2 ? -P.ca4 : ka3));
+    const double u = fma(ua, ub, uc);
+    const double gm = shfl(u, gl.base + 0) * shfl(u, gl.base + (gl.comp < 3 ? 1 : 2));
+    const double kcs = shfl(u, gl.base + 3 + (gl.comp < 3 ? gl.comp : 0));
+    const double kc = gl.comp < 3 ? kcs : 0.0;
     const double q = gm * dj;
     r2out = r2;
     d3[0] = d0;

@@ -145,3 +145,22 @@ def test_autotuner_picks_a_valid_configuration(torch_cuda):
         a, b = Bd.to_numpy(a), Bd.to_numpy(b)
         for k in a:
             np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+def test_launch_phases_are_ordered_and_bounded(torch_cuda):
+    """The device-clock phase times of a persistent launch: 0 < lane phase <= total <= event time,
+    on the system's own scratch and on a caller's scratch."""
+    torch = torch_cuda
+    systems, y0, phi0, sid = I.c1_workload(16)
+    with Bd.System([s.as_dict() for s in systems]) as S:
+        y, p, d = Bd.to_device_soa(y0, phi0, sid)
+        for scratch in (None, torch.zeros(Bd.ia_scratch_bytes(len(phi0)) // 8 + 32, dtype=torch.float64,
+                                          device="cuda")):
+            out = Bd.alloc_obs(len(phi0))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            Bd.ia_launch(S.handle, y, p, d, out, scratch=scratch)
+            e1.record()
+            torch.cuda.synchronize()
+            lane_ms, total_ms = Bd.ia_launch_phases(S.handle, scratch)
+            assert 0.0 < lane_ms <= total_ms <= e0.elapsed_time(e1) * 1.05 + 0.1
