@@ -64,6 +64,7 @@ def parse():
     p.add_argument("--tail-group", type=int, default=0)
     p.add_argument("--tail-blocks-per-sm", type=int, default=0)
     p.add_argument("--tail-sms", type=int, default=0)
+    p.add_argument("--tail-pair", type=int, default=0, help="1/0: paired tail warps (default), -1: off")
     p.add_argument("--diff-sample", type=int, default=4096,
                    help="trajectories of the differentiation workload timed through the tangent and adjoint "
                         "kernels (0: skip)")
@@ -315,7 +316,7 @@ def main():
     stream = torch.cuda.current_stream()
     kw = {"block": args.block, "refill": args.refill, "blocks_per_sm": args.blocks_per_sm,
           "regs_variant": args.regs_variant, "slice_budget": args.slice_budget, "tail_group": args.tail_group,
-          "tail_blocks_per_sm": args.tail_blocks_per_sm, "tail_sms": args.tail_sms}
+          "tail_blocks_per_sm": args.tail_blocks_per_sm, "tail_sms": args.tail_sms, "tail_pair": args.tail_pair}
 
     # every step's inputs in pinned host memory and its device buffers (generation outside the timing)
     steps = []
@@ -368,7 +369,7 @@ def main():
     barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
-    lane_ms, dev_ms = Bd.ia_launch_phases(sysh.handle)  # the last step's launch
+    lane_ms, dev_ms, wait_errors = Bd.ia_launch_phases(sysh.handle)  # the last step's launch
     kern_ms = [e[1].elapsed_time(e[2]) for e in ev]
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     total_ms = float(sum(kern_ms))
@@ -378,6 +379,8 @@ def main():
     per = (outs[0]["n_steps"].to(torch.int64) + outs[0]["n_rej"].to(torch.int64)).cpu().numpy()
     max_attempts = int(max(int((o["n_steps"] + o["n_rej"]).max().item()) for o in outs))
     longest = int(np.argmax(per))
+    budget_used = args.slice_budget if args.slice_budget > 0 else 65536
+    long_counts = {f"over_{b}": int((per > b).sum()) for b in (budget_used, 262144, 1048576)}
     longest_pos = int(np.nonzero(steps[0]["order"] == longest)[0][0])
     rhs = 6 * attempts + n_local
     tmax_ms, emax_ms = total_ms, float(sum(step_ms))
@@ -444,12 +447,13 @@ def main():
                 "l2": "256 MiB buffer written before each step (inputs < L2)",
                 "block": args.block or 128, "refill": args.refill or 1,
                 "slice_budget": args.slice_budget or 65536, "tail_group": args.tail_group or 6,
-                "tail_sms": args.tail_sms or 8,
+                "tail_sms": args.tail_sms or 8, "tail_pair": args.tail_pair >= 0 and (args.tail_group or 6) == 6,
             },
             "rhs_evals_per_s": rhs_all / (tmax_ms / 1e3),
             "attempted_steps_per_trajectory": att_all / n_all,
             "max_attempted_steps": max_attempts,
             "longest_trajectory_queue_position": longest_pos / steps[0]["n"],
+            "long_trajectories_step0": long_counts,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_flops / 1e12,
                          "unit": "TFLOP/s", "frac": achieved / peak_flops, "traffic": None,
                          "peak_source": "FP64 FMA microbenchmark (ia_fp64_peak) measured in this run",
@@ -457,7 +461,7 @@ def main():
             "plain": plain,
             "e2e": e2e,
             "gpu_launches": args.steps * (1 if args.slice_budget < 0 else 2),
-            "phases_last_step": {"lane_phase_ms": lane_ms, "kernel_ms": dev_ms,
+            "phases_last_step": {"lane_phase_ms": lane_ms, "kernel_ms": dev_ms, "wait_errors": wait_errors,
                                  "note": "device clock: until the last warp left the lane phase (every "
                                          "trajectory started; long ones handed to group mode) / until the "
                                          "last warp finished"},

@@ -121,6 +121,10 @@ typedef struct ia_launch_opts {
     int32_t tail_blocks_per_sm; /* blocks (128 threads) per SM of the clean-up tail kernel, 1..16; 0 = 1 */
     int32_t tail_sms;           /* persistent: SMs whose single block works on suspended trajectories from
                                    the start, 1..192; 0 = 8; -1 = none */
+    int32_t tail_pair;          /* persistent, tail_group 6: on the reserved SMs, two warps on two sub-
+                                   partitions advance the same trajectories together (about twice the
+                                   step rate of one warp; bit-identical results): 0 or 1 = on, -1 = off */
+    int32_t reserved;           /* must be 0 */
     int64_t suspend_capacity;   /* suspend records; 0 = min(n, max(4096, n/32)). A trajectory that finds
                                    no free record is finished by its lane. */
     void* scratch;              /* persistent: caller's device scratch (256-byte aligned), or NULL to use
@@ -198,12 +202,14 @@ int ia_launch_static(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_ob
  * Phase times of the last persistent launch whose scratch is `scratch` (NULL: the system's own
  * scratch), from the device clock: *lane_ms = from the first block's start until the last warp left
  * the lane phase (every trajectory had started and had either finished or been handed to the tail
- * phase), *total_ms = until the last warp finished. Synchronous (copies 64 bytes from the device; call
- * it after the launch completed). A diagnostic of how a batch's time splits between the bulk of short
- * trajectories and the long-lived complexes; no counterpart in the paper. IA_ERR_INVALID_ARG if that
- * scratch holds no completed persistent launch.
+ * phase), *total_ms = until the last warp finished. *errors (if not NULL) = bounded waits of that
+ * launch that ran out (0 in a healthy run; otherwise some trajectories may have no result).
+ * Synchronous (copies the launch's counters from the device; call it after the launch completed).
+ * A diagnostic of how a batch's time splits between the bulk of short trajectories and the
+ * long-lived complexes; no counterpart in the paper. IA_ERR_INVALID_ARG if that scratch holds no
+ * completed persistent launch.
  */
-int ia_launch_phases(ia_system* sys, const void* scratch, double* lane_ms, double* total_ms);
+int ia_launch_phases(ia_system* sys, const void* scratch, double* lane_ms, double* total_ms, int64_t* errors);
 
 /*
  * FP64 FMA throughput microbenchmark (no counterpart in the paper: it measures the roofline

@@ -81,8 +81,8 @@ class ia_launch_opts(ctypes.Structure):
                 ("refill", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("regs_variant", ctypes.c_int32), ("slice_budget", ctypes.c_int32),
                 ("tail_group", ctypes.c_int32), ("tail_blocks_per_sm", ctypes.c_int32),
-                ("tail_sms", ctypes.c_int32), ("suspend_capacity", ctypes.c_int64),
-                ("scratch", ctypes.c_void_p), ("scratch_bytes", ctypes.c_int64)]
+                ("tail_sms", ctypes.c_int32), ("tail_pair", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("suspend_capacity", ctypes.c_int64), ("scratch", ctypes.c_void_p), ("scratch_bytes", ctypes.c_int64)]
 
 
 class ia_tangent_in(ctypes.Structure):
@@ -154,7 +154,8 @@ def load(build_if_missing: bool = True):
     L.ia_launch_tangent.argtypes = [ctypes.c_void_p, P(ia_ic_soa), ctypes.c_int64, P(ia_obs_soa),
                                     P(ia_tangent_in), P(ia_tangent_out), ctypes.c_void_p]
     L.ia_launch_tangent.restype = ctypes.c_int
-    L.ia_launch_phases.argtypes = [ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_double), P(ctypes.c_double)]
+    L.ia_launch_phases.argtypes = [ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_double), P(ctypes.c_double),
+                                   P(ctypes.c_int64)]
     L.ia_launch_phases.restype = ctypes.c_int
     L.ia_adjoint_scratch_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int64, P(ia_adjoint_opts)]
     L.ia_adjoint_scratch_bytes.restype = ctypes.c_int64
@@ -272,7 +273,7 @@ def to_device_soa(y0, phi0, sys_id=None, device="cuda"):
 def make_opts(kernel: int = IA_KERNEL_PERSISTENT, block: int = 0, grid: int = 0, refill: int = 0,
               blocks_per_sm: int = 0, regs_variant: int = 0, slice_budget: int = 0, tail_group: int = 0,
               tail_blocks_per_sm: int = 0, suspend_capacity: int = 0, scratch=None,
-              tail_sms: int = 0) -> ia_launch_opts:
+              tail_sms: int = 0, tail_pair: int = 0) -> ia_launch_opts:
     opts = ia_launch_opts()
     opts.kernel = kernel
     opts.block = block
@@ -285,6 +286,7 @@ def make_opts(kernel: int = IA_KERNEL_PERSISTENT, block: int = 0, grid: int = 0,
     opts.tail_blocks_per_sm = tail_blocks_per_sm
     opts.suspend_capacity = suspend_capacity
     opts.tail_sms = tail_sms
+    opts.tail_pair = tail_pair
     if scratch is not None:
         opts.scratch = scratch.data_ptr()
         opts.scratch_bytes = scratch.numel() * scratch.element_size()
@@ -444,12 +446,12 @@ def ia_launch_tangent(handle: int, y0_soa, phi0, sys_id, out: dict, dy0, dq, tan
 
 
 def ia_launch_phases(handle: int, scratch=None) -> tuple:
-    """(lane-phase ms, total ms) of the last persistent launch on `scratch` (a device tensor) or on
-    the system's own scratch; synchronous."""
-    a, b = ctypes.c_double(), ctypes.c_double()
+    """(lane-phase ms, total ms, bounded waits that ran out) of the last persistent launch on
+    `scratch` (a device tensor) or on the system's own scratch; synchronous."""
+    a, b, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
     _check(load().ia_launch_phases(handle, scratch.data_ptr() if scratch is not None else None,
-                                   ctypes.byref(a), ctypes.byref(b)))
-    return a.value, b.value
+                                   ctypes.byref(a), ctypes.byref(b), ctypes.byref(e)))
+    return a.value, b.value, e.value
 
 
 OBJECTIVES = ("theta_s", "dp", "dE_ion", "t_final")

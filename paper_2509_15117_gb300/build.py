@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libionatom.so")
 SOURCES = [os.path.join(CSRC, "ia_capi.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("ia_traj.cuh", "dp5_nystrom.h")] + [
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".cuh", ".h"))] + [
     os.path.join(ROOT, "include", "ionatom.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-shared", *ARCH]

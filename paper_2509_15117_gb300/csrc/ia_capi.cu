@@ -388,6 +388,437 @@ __device__ __forceinline__ void tail_phase(const SysDev* __restrict__ tab, const
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Paired tail phase. An FP64 instruction occupies a sub-partition's FP64 unit for its whole issue
+// time whatever the number of active lanes, so the latency of one trajectory in group mode is its
+// FP64 instruction count per step. Here the two warps of a pair -- on two sub-partitions, each with
+// its own FP64 unit -- advance the same five trajectories together: the chain warp runs the serial
+// part of every stage (the last term of the stage position and the force), the helper warp the rest
+// (step coefficients, rf phases, ion trap coefficients, position partial sums, new velocity, error
+// estimate, accept/reject decision, exit epilogue and result). Every value is formed with the
+// expressions of the other layouts, so the results are bit-identical to them. The warps exchange
+// data through shared memory, lane by lane: each lane reads only the slots of its counterpart lane,
+// which publishes them with a per-lane sequence counter (release / acquire at block scope); every wait
+// is bounded, and when one runs out both warps leave the tail phase and count an error (the clean-up
+// kernel cannot resume a trajectory a pair held, so the host sees the error count).
+
+struct __align__(16) PairShared {
+    double a[8][32];    // chain -> helper: a_l of stage l
+    double xp[8][32];   // helper -> chain: X3 (slot 3) and the partial positions of stages 4..7
+    double kc[8][32];   // helper -> chain: ka_j + kq_j cos(Omega t_l + phi0) of stage l (ion lanes)
+    double w[4][32];    // helper -> chain: w42, w53, w64, w75
+    double xn[32];      // chain -> helper: X7, the position at the step end
+    double dn[3][32];   // chain -> helper: separation at X7
+    double r2n[32];     // chain -> helper: its square
+    double vn[32];      // helper -> chain: velocity at the step end
+    double rd[32];      // helper -> chain: d . (v_a - v_i) at the step end
+    long long ck[32];   // helper -> chain: claimed suspend record of the lane's group
+    float errf[32];     // helper -> chain: error ratio of the lane's group
+    int dec[32];        // helper -> chain: bit 0 accept, bit 1 finite
+    int claim[32];      // helper -> chain: claim result of the lane's group (0..3, as in tail_phase)
+    unsigned long long seq_h[32], seq_c[32];  // posts of the helper and of the chain warp, per lane
+};
+
+constexpr unsigned PAIR_SPIN_LIMIT = 1u << 26;  // a partner that stopped answering: seconds
+
+__device__ __forceinline__ void st_release_cta(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.release.cta.shared::cta.u64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "l"(v)
+                 : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_cta(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.cta.shared::cta.u64 %0, [%1];"
+                 : "=l"(v)
+                 : "r"((unsigned)__cvta_generic_to_shared(p))
+                 : "memory");
+    return v;
+}
+// Each lane of the consumer reads only the slots its own lane of the producer wrote, so every lane
+// synchronises with its counterpart directly: the producer lane writes its data, then its counter
+// (release); the consumer lane waits for its counterpart's counter (acquire), then reads.
+__device__ __forceinline__ void pair_post(unsigned long long* seq, unsigned long long& n)
+{
+    ++n;
+    st_release_cta(seq + (threadIdx.x & 31), n);
+}
+// Consumer: false (in every lane) when a counterpart did not post within the bound.
+__device__ __forceinline__ bool pair_wait(const unsigned long long* seq, unsigned long long& n)
+{
+    ++n;
+    const unsigned long long* mine = seq + (threadIdx.x & 31);
+    unsigned spins = 0;
+    bool ok = true;
+    while (ld_acquire_cta(mine) < n) {
+        if (++spins > PAIR_SPIN_LIMIT) {
+            ok = false;
+            break;
+        }
+        if (spins > 256) __nanosleep(64);
+    }
+    return __all_sync(FULL, ok);
+}
+
+// Interaction part of a stage acceleration (everything of accel_group<6> but the ion trap term):
+// returns gm d_j; the acceleration is fma(kc, p, returned value) with kc the trap coefficient.
+__device__ __forceinline__ double chain_force(const SysDev& P, const GroupLane<6>& gl, double p, double& r2out,
+                                              double d3[3])
+{
+    const int j = gl.comp < 3 ? gl.comp : gl.comp - 3;
+    const double pi = shfl(p, gl.base + j);
+    const double pa = shfl(p, gl.base + 3 + j);
+    const double dj = pa - pi;
+    const double d0 = shfl(dj, gl.base + 0), d1 = shfl(dj, gl.base + 1), d2 = shfl(dj, gl.base + 2);
+    const double r2 = fma(d0, d0, fma(d1, d1, d2 * d2));
+    const double s = rcp_nr(r2);
+    const double s2 = s * s;
+    // one FMA instruction: lane 0 forms s2 s, lane 1 the ion's ci8 s2 - ci4, lane 2 the atom's
+    const int c = gl.c;
+    const double ua = c == 0 ? s2 : (c == 1 ? P.ci8 : P.ca8);
+    const double ub = c == 0 ? s : s2;
+    const double uc = c == 0 ? 0.0 : (c == 1 ? -P.ci4 : -P.ca4);
+    const double u = fma(ua, ub, uc);
+    const double gm = shfl(u, gl.base + 0) * shfl(u, gl.base + (gl.comp < 3 ? 1 : 2));
+    r2out = r2;
+    d3[0] = d0;
+    d3[1] = d1;
+    d3[2] = d2;
+    return gm * dj;
+}
+
+__device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, const IcPtrs& ic, const ObsPtrs& out,
+                                                const Susp* __restrict__ susp, const unsigned* __restrict__ ready,
+                                                Counters* __restrict__ ctr, long long cap,
+                                                unsigned long long total_warps, PairShared* sh, bool helper)
+{
+    constexpr int G = 6;
+    constexpr int R = (N_COEF + G - 1) / G;
+    const GroupLane<G> gl = group_lane<G>();
+    const int lane = threadIdx.x & 31;
+    // idle groups keep a harmless state (unit separation) so that their arithmetic stays on the fast path
+    double x = gl.comp < 3 ? 0.0 : 1.0, v = 0.0, a1 = 0.0;
+    Scal S;
+    S.t = 0.0; S.h = 1.0; S.hmin = 0.0; S.phi0 = 0.0; S.rdot_prev = 0.0; S.t_first = 0.0; S.t_last = 0.0;
+    S.n_acc = 0; S.n_rej = 0; S.n_bounce = 0; S.nofailed = true; S.retry = false;
+    long long idx = -1;
+    int sid = 0;
+    bool active = false, drained = false, broken = false;
+    unsigned idle_spins = 0, claim_skip = 0;
+    unsigned long long nh = 0, nc = 0;  // posts seen / made in each direction
+    for (;;) {
+        const bool need = !active && !drained;
+        bool poll = __any_sync(FULL, need);
+        if (poll && claim_skip > 0 && __any_sync(FULL, active)) {
+            --claim_skip;
+            poll = false;
+        }
+        if (poll) {
+            // the helper claims for the idle groups and publishes; the chain warp acknowledges
+            int got = 0;
+            unsigned long long k = 0;
+            if (helper) {
+                if (need && gl.c == 0) {
+                    if (claim_record(ctr, cap, k)) {
+                        got = 1;
+                        unsigned spins = 0;
+                        while (*(volatile const unsigned*)(ready + k) == 0u) {
+                            if (++spins > READY_SPIN_LIMIT) {
+                                atomicAdd(&ctr->errors, 1ull);
+                                got = 0;
+                                break;
+                            }
+                            __nanosleep(256);
+                        }
+                        __threadfence();
+                    } else {
+                        const bool lane_work_left =
+                            *(volatile unsigned long long*)&ctr->warps_done < total_warps;
+                        got = lane_work_left ? 2 : 3;
+                        if (got == 3 && claim_record(ctr, cap, k)) {
+                            got = 1;
+                            unsigned spins = 0;
+                            while (*(volatile const unsigned*)(ready + k) == 0u) {
+                                if (++spins > READY_SPIN_LIMIT) {
+                                    atomicAdd(&ctr->errors, 1ull);
+                                    got = 0;
+                                    break;
+                                }
+                                __nanosleep(256);
+                            }
+                            __threadfence();
+                        }
+                    }
+                }
+                got = __shfl_sync(FULL, got, gl.base);
+                k = __shfl_sync(FULL, k, gl.base);
+                sh->claim[lane] = got;
+                sh->ck[lane] = (long long)k;
+                pair_post(sh->seq_h, nh);
+                if (!pair_wait(sh->seq_c, nc)) broken = true;
+            } else {
+                if (!pair_wait(sh->seq_h, nh)) {
+                    broken = true;
+                } else {
+                    got = sh->claim[lane];
+                    k = (unsigned long long)sh->ck[lane];
+                    pair_post(sh->seq_c, nc);
+                }
+            }
+            if (broken) break;
+            if (!__any_sync(FULL, need && got == 1)) claim_skip = CLAIM_BACKOFF;
+            if (need) {
+                if (got == 1) {
+                    const Susp* r = susp + k;
+                    x = __ldcg(&r->x[gl.comp]);
+                    v = __ldcg(&r->v[gl.comp]);
+                    a1 = __ldcg(&r->a1[gl.comp]);
+                    S.t = __ldcg(&r->t); S.h = __ldcg(&r->h); S.phi0 = __ldcg(&r->phi0);
+                    S.rdot_prev = __ldcg(&r->rdot_prev);
+                    S.t_first = __ldcg(&r->t_first); S.t_last = __ldcg(&r->t_last);
+                    S.n_acc = __ldcg(&r->n_acc); S.n_rej = __ldcg(&r->n_rej); S.n_bounce = __ldcg(&r->n_bounce);
+                    const int flags = __ldcg(&r->flags);
+                    S.nofailed = (flags & 1) != 0;
+                    S.retry = (flags & 2) != 0;
+                    S.hmin = hmin_at(S.t);
+                    idx = __ldcg(&r->idx);
+                    sid = __ldcg(&r->sid);
+                    active = true;
+                } else if (got == 3) {
+                    drained = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, active)) {
+            if (__all_sync(FULL, drained)) break;
+            if (++idle_spins > IDLE_SPIN_LIMIT) {
+                if (lane == 0 && helper) atomicAdd(&ctr->errors, 1ull);
+                break;
+            }
+            __nanosleep(1000);
+            continue;
+        }
+
+        const SysDev& P = tab[sid];
+        uint32_t st = 0xffffffffu;
+        if (active) st = attempt_begin(P, S);
+        const double h = S.h, t = S.t;
+        // values both warps hold at the end of the attempt
+        double xn, vn, a7, r2new, rd;
+        double a3 = 0.0, a4 = 0.0, a5 = 0.0, a6 = 0.0;  // helper: kept for the exit epilogue
+        float errf;
+        bool accept, finite;
+        if (helper) {
+            Coef K;
+            K.h2 = h * h;
+            double cv[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int kk = r * G + gl.c < N_COEF ? r * G + gl.c : N_COEF - 1;
+                cv[r] = COEF_K[kk] * (COEF_H2[kk] ? K.h2 : h);
+            }
+            {
+                double* kp = &K.c2;
+#pragma unroll
+                for (int k = 0; k < N_COEF; ++k) kp[k] = shfl(cv[k / G], gl.base + (k % G));
+            }
+            const double chsel = gl.c < 4 ? cv[0] : h;
+            const double cl = cos(fma(P.Omega, t + chsel, S.phi0));
+            const double cs2 = shfl(cl, gl.base + 0), cs3 = shfl(cl, gl.base + 1), cs4 = shfl(cl, gl.base + 2);
+            const double cs5 = shfl(cl, gl.base + 3), cs67 = shfl(cl, gl.base + 4);
+            const double kqj = gl.comp < 3 ? P.kq[gl.comp] : 0.0;
+            const double kaj = gl.comp < 3 ? P.ka[gl.comp] : 0.0;
+            sh->kc[2][lane] = fma(kqj, cs2, kaj);
+            sh->kc[3][lane] = fma(kqj, cs3, kaj);
+            sh->kc[4][lane] = fma(kqj, cs4, kaj);
+            sh->kc[5][lane] = fma(kqj, cs5, kaj);
+            sh->kc[6][lane] = fma(kqj, cs67, kaj);
+            sh->w[0][lane] = K.w42;
+            sh->w[1][lane] = K.w53;
+            sh->w[2][lane] = K.w64;
+            sh->w[3][lane] = K.w75;
+            sh->xp[3][lane] = pos3(K, x, v, a1);
+            sh->xp[4][lane] = fma(K.w41, a1, fma(K.c4, v, x));
+            pair_post(sh->seq_h, nh);                                     // H1
+            double p5 = fma(K.w51, a1, fma(K.c5, v, x));
+            double p6 = fma(K.w61, a1, fma(h, v, x));
+            double p7 = fma(K.w71, a1, fma(h, v, x));
+            double vacc = fma(K.b1, a1, v);
+            double ex = K.f1 * a1, ev = K.e1 * a1;
+            bool ok = pair_wait(sh->seq_c, nc);                           // C1: a2
+            const double a2 = sh->a[2][lane];
+            p5 = fma(K.w52, a2, p5);
+            sh->xp[5][lane] = p5;
+            pair_post(sh->seq_h, nh);                                     // H2
+            p6 = fma(K.w62, a2, p6);
+            ok = pair_wait(sh->seq_c, nc) && ok;                          // C2: a3
+            a3 = sh->a[3][lane];
+            p6 = fma(K.w63, a3, p6);
+            sh->xp[6][lane] = p6;
+            pair_post(sh->seq_h, nh);                                     // H3
+            p7 = fma(K.w73, a3, p7);
+            vacc = fma(K.b3, a3, vacc);
+            ex = fma(K.f3, a3, ex);
+            ev = fma(K.e3, a3, ev);
+            ok = pair_wait(sh->seq_c, nc) && ok;                          // C3: a4
+            a4 = sh->a[4][lane];
+            p7 = fma(K.w74, a4, p7);
+            sh->xp[7][lane] = p7;
+            pair_post(sh->seq_h, nh);                                     // H4
+            vacc = fma(K.b4, a4, vacc);
+            ex = fma(K.f4, a4, ex);
+            ev = fma(K.e4, a4, ev);
+            ok = pair_wait(sh->seq_c, nc) && ok;                          // C4: a5
+            a5 = sh->a[5][lane];
+            vacc = fma(K.b5, a5, vacc);
+            ex = fma(K.f5, a5, ex);
+            ev = fma(K.e5, a5, ev);
+            ok = pair_wait(sh->seq_c, nc) && ok;                          // C5: a6
+            a6 = sh->a[6][lane];
+            vn = fma(K.b6, a6, vacc);
+            ex = fma(K.f6, a6, ex);
+            ev = fma(K.e6, a6, ev);
+            ok = pair_wait(sh->seq_c, nc) && ok;                          // C6: a7 and the step end
+            a7 = sh->a[7][lane];
+            xn = sh->xn[lane];
+            r2new = sh->r2n[lane];
+            const double dn0 = sh->dn[0][lane], dn1 = sh->dn[1][lane], dn2 = sh->dn[2][lane];
+            ev = fma(K.e7, a7, ev);
+            bool okx, fx, okv, fv;
+            float rx, rv;
+            err_check(P.rtol, P.atol_pos, x, xn, ex, okx, fx, rx);
+            err_check(P.rtol, P.atol_vel, v, vn, ev, okv, fv, rv);
+            const bool real = gl.c < 6;
+            const bool okk = !real || (okx && okv);
+            const bool fi = !real || (fx && fv);
+            const float ratio = real ? fmaxf(rx, rv) : 0.0f;
+            const unsigned gmask = ((1u << G) - 1u) << gl.base;
+            accept = (__ballot_sync(FULL, !okk) & gmask) == 0;
+            finite = (__ballot_sync(FULL, !fi) & gmask) == 0;
+            errf = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) errf = fmaxf(errf, __shfl_sync(FULL, ratio, gl.base + k));
+            const int j = gl.comp < 3 ? gl.comp : gl.comp - 3;
+            const double wj = shfl(vn, gl.base + 3 + j) - shfl(vn, gl.base + j);
+            const double w0 = shfl(wj, gl.base + 0), w1 = shfl(wj, gl.base + 1), w2 = shfl(wj, gl.base + 2);
+            rd = fma(dn0, w0, fma(dn1, w1, dn2 * w2));
+            sh->vn[lane] = vn;
+            sh->rd[lane] = rd;
+            sh->errf[lane] = errf;
+            sh->dec[lane] = (accept ? 1 : 0) | (finite ? 2 : 0);
+            pair_post(sh->seq_h, nh);                                     // H5
+            if (!ok) broken = true;
+        } else {
+            // stage 2
+            const double X2 = fma(COEF_K[0] * h, v, x);
+            double r2, d3[3];
+            const double q2 = chain_force(P, gl, X2, r2, d3);
+            bool ok = pair_wait(sh->seq_h, nh);                           // H1
+            const double a2 = fma(gl.comp < 3 ? sh->kc[2][lane] : 0.0, X2, q2);
+            sh->a[2][lane] = a2;
+            pair_post(sh->seq_c, nc);                                     // C1
+            // stage 3
+            const double X3 = sh->xp[3][lane];
+            const double c3 = fma(gl.comp < 3 ? sh->kc[3][lane] : 0.0, X3, chain_force(P, gl, X3, r2, d3));
+            sh->a[3][lane] = c3;
+            pair_post(sh->seq_c, nc);                                     // C2
+            // stage 4
+            const double X4 = fma(sh->w[0][lane], a2, sh->xp[4][lane]);
+            const double c4 = fma(gl.comp < 3 ? sh->kc[4][lane] : 0.0, X4, chain_force(P, gl, X4, r2, d3));
+            sh->a[4][lane] = c4;
+            pair_post(sh->seq_c, nc);                                     // C3
+            // stage 5
+            ok = pair_wait(sh->seq_h, nh) && ok;                          // H2
+            const double X5 = fma(sh->w[1][lane], c3, sh->xp[5][lane]);
+            const double c5 = fma(gl.comp < 3 ? sh->kc[5][lane] : 0.0, X5, chain_force(P, gl, X5, r2, d3));
+            sh->a[5][lane] = c5;
+            pair_post(sh->seq_c, nc);                                     // C4
+            // stage 6
+            ok = pair_wait(sh->seq_h, nh) && ok;                          // H3
+            const double X6 = fma(sh->w[2][lane], c4, sh->xp[6][lane]);
+            const double c6 = fma(gl.comp < 3 ? sh->kc[6][lane] : 0.0, X6, chain_force(P, gl, X6, r2, d3));
+            sh->a[6][lane] = c6;
+            pair_post(sh->seq_c, nc);                                     // C5
+            // stage 7: the step end
+            ok = pair_wait(sh->seq_h, nh) && ok;                          // H4
+            xn = fma(sh->w[3][lane], c5, sh->xp[7][lane]);
+            double dn[3];
+            a7 = fma(gl.comp < 3 ? sh->kc[6][lane] : 0.0, xn, chain_force(P, gl, xn, r2new, dn));
+            sh->a[7][lane] = a7;
+            sh->xn[lane] = xn;
+            sh->r2n[lane] = r2new;
+            sh->dn[0][lane] = dn[0];
+            sh->dn[1][lane] = dn[1];
+            sh->dn[2][lane] = dn[2];
+            pair_post(sh->seq_c, nc);                                     // C6
+            ok = pair_wait(sh->seq_h, nh) && ok;                          // H5: the decision
+            vn = sh->vn[lane];
+            rd = sh->rd[lane];
+            errf = sh->errf[lane];
+            const int dec = sh->dec[lane];
+            accept = (dec & 1) != 0;
+            finite = (dec & 2) != 0;
+            if (!ok) broken = true;
+        }
+        if (broken) break;
+
+        int res = 0;  // 0 running, 1 stopped, 2 exits in this step
+        if (active) {
+            if (st != 0xffffffffu) {
+                res = 1;
+            } else if (!finite) {
+                res = 1;
+                st = ST_NONFINITE;
+            } else if (!accept) {
+                st = on_reject(P, S, errf);
+                if (st != 0xffffffffu) res = 1;
+            } else if (on_accept(P, S, rd, r2new)) {
+                res = 2;
+            } else {
+                x = xn;
+                v = vn;
+                a1 = a7;
+                on_commit(P, S, errf);
+            }
+        }
+        if (__any_sync(FULL, res != 0)) {
+            if (helper) {
+                Final fin;
+                fin.t = S.t;
+                fin.status = st;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    fin.xi[k] = shfl(x, gl.base + k);
+                    fin.xa[k] = shfl(x, gl.base + 3 + k);
+                    fin.vi[k] = shfl(v, gl.base + k);
+                    fin.va[k] = shfl(v, gl.base + 3 + k);
+                }
+                if (__any_sync(FULL, res == 2)) {
+                    StepData D;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        D.xi[k] = fin.xi[k]; D.xa[k] = fin.xa[k]; D.vi[k] = fin.vi[k]; D.va[k] = fin.va[k];
+                        D.a1i[k] = shfl(a1, gl.base + k); D.a1a[k] = shfl(a1, gl.base + 3 + k);
+                        D.a3i[k] = shfl(a3, gl.base + k); D.a3a[k] = shfl(a3, gl.base + 3 + k);
+                        D.a4i[k] = shfl(a4, gl.base + k); D.a4a[k] = shfl(a4, gl.base + 3 + k);
+                        D.a5i[k] = shfl(a5, gl.base + k); D.a5a[k] = shfl(a5, gl.base + 3 + k);
+                        D.a6i[k] = shfl(a6, gl.base + k); D.a6a[k] = shfl(a6, gl.base + 3 + k);
+                        D.a7i[k] = shfl(a7, gl.base + k); D.a7a[k] = shfl(a7, gl.base + 3 + k);
+                        D.xni[k] = shfl(xn, gl.base + k); D.xna[k] = shfl(xn, gl.base + 3 + k);
+                        D.vni[k] = shfl(vn, gl.base + k); D.vna[k] = shfl(vn, gl.base + 3 + k);
+                    }
+                    D.h = h;
+                    D.t = t;
+                    if (res == 2 && gl.c == 0) finish_exit(P, D, r2new, fin);
+                }
+                if (res != 0 && gl.c == 0) store_result(P, ic, out, idx, tally(S), fin, true);
+            }
+            if (res != 0) active = false;
+        }
+    }
+    if (broken && lane == 0) atomicAdd(&ctr->errors, 1ull);
+}
+
 // Fused persistent kernel. Blocks on SMs with id < tail_sms (one block per such SM) are tail
 // workers from the start, so long-lived complexes run in group mode on sub-partitions of their own
 // while the rest of the GPU works through the queue; every other block runs the lane phase and then
@@ -397,10 +828,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sched(const SysDev* __restrict_
                                                        ObsPtrs out, long long n, Counters* __restrict__ ctr,
                                                        unsigned* __restrict__ ready, Susp* __restrict__ susp,
                                                        long long cap, int refill, int budget, int tail_sms,
-                                                       int wait_ok)
+                                                       int wait_ok, int pair)
 {
     __shared__ int role;  // 0 lane phase first, 1 tail worker, 2 surplus block on a reserved SM
+    __shared__ PairShared pair_sh[G == 6 ? BLOCK / 64 : 1];
     if (threadIdx.x == 0) {
+        for (int k = 0; k < (G == 6 ? BLOCK / 64 : 1); ++k)
+            for (int l = 0; l < 32; ++l) pair_sh[k].seq_h[l] = pair_sh[k].seq_c[l] = 0ull;
         atomicCAS(&ctr->t_start, 0ull, global_ns());
         int r = 0;
         if (budget > 0 && tail_sms > 0) {
@@ -419,7 +853,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sched(const SysDev* __restrict_
         __threadfence();
         if (atomicAdd(&ctr->warps_done, 1ull) + 1ull == total_warps) atomicMax(&ctr->t_lane_end, global_ns());
     }
-    if (r != 2 && budget > 0) tail_phase<G>(tab, ic, out, susp, ready, ctr, cap, wait_ok != 0, total_warps);
+    if (G == 6 && r == 1 && pair && wait_ok) {
+        // dedicated tail block: warps 2p and 2p+1 form pair p (chain and helper warp)
+        const int w = threadIdx.x >> 5;
+        tail_phase_pair(tab, ic, out, susp, ready, ctr, cap, total_warps, &pair_sh[G == 6 ? (w >> 1) : 0],
+                        (w & 1) != 0);
+    } else if (r != 2 && budget > 0) {
+        tail_phase<G>(tab, ic, out, susp, ready, ctr, cap, wait_ok != 0, total_warps);
+    }
     if ((threadIdx.x & 31) == 0) atomicMax(&ctr->t_end, global_ns());
 }
 
@@ -871,6 +1312,7 @@ int resolve(int64_t n, const ia_launch_opts* opts, Resolved& r)
     if (o.refill == 0) o.refill = 1;
     if (o.refill < 1 || o.refill > 32) return IA_ERR_INVALID_ARG;
     if (o.grid < 0 || o.blocks_per_sm < 0 || o.tail_blocks_per_sm < 0) return IA_ERR_INVALID_ARG;
+    if (o.tail_pair < -1 || o.tail_pair > 1 || o.reserved != 0) return IA_ERR_INVALID_ARG;
     if (o.slice_budget == 0) o.slice_budget = DEFAULT_BUDGET;
     if (o.slice_budget < -1) return IA_ERR_INVALID_ARG;
     if (o.tail_group == 0) o.tail_group = 6;
@@ -1085,8 +1527,10 @@ int ia_launch(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* 
     int refill = o.refill;
     int n_sys = sys->n_sys;
     const SysDev* tab = sys->d_tab;
+    int pair = (o.tail_group != 8 && o.tail_pair >= 0) ? 1 : 0;
     void* args[] = {(void*)&tab, (void*)&n_sys, (void*)&icp, (void*)&op, (void*)&nn, (void*)&ctr, (void*)&ready,
-                    (void*)&susp, (void*)&cap, (void*)&refill, (void*)&budget, (void*)&tail_sms, (void*)&wait_ok};
+                    (void*)&susp, (void*)&cap, (void*)&refill, (void*)&budget, (void*)&tail_sms, (void*)&wait_ok,
+                    (void*)&pair};
     cudaError_t e;
     if (wait_ok)
         e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, st);
@@ -1278,12 +1722,12 @@ int ia_autotune(ia_system* sys, const ia_ic_soa* ic, int64_t n, int32_t attempt_
         }
         int grid = resident * sys->num_sms;
         long long nn_ = (long long)n;
-        int refill = cd.refill, budget = attempt_cap, tail_sms = 0, wait_ok = 0, n_sys = sys->n_sys;
+        int refill = cd.refill, budget = attempt_cap, tail_sms = 0, wait_ok = 0, pair = 0, n_sys = sys->n_sys;
         long long capv = cap;
         const SysDev* tab = sys->d_tab;
         void* args[] = {(void*)&tab, (void*)&n_sys, (void*)&icp, (void*)&op, (void*)&nn_, (void*)&ctr,
                         (void*)&ready, (void*)&susp, (void*)&capv, (void*)&refill, (void*)&budget,
-                        (void*)&tail_sms, (void*)&wait_ok};
+                        (void*)&tail_sms, (void*)&wait_ok, (void*)&pair};
         if (cudaMemsetAsync(scr, 0, SCRATCH_HEAD + ready_bytes(cap), st) != cudaSuccess) rc = IA_ERR_CUDA;
         cudaEventRecord(e0, st);
         // budget > 0 with no tail workers: the kernel stops every trajectory at the cap
@@ -1487,7 +1931,7 @@ int ia_launch_adjoint(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_o
     return cudaGetLastError() == cudaSuccess ? IA_OK : IA_ERR_CUDA;
 }
 
-int ia_launch_phases(ia_system* sys, const void* scratch, double* lane_ms, double* total_ms)
+int ia_launch_phases(ia_system* sys, const void* scratch, double* lane_ms, double* total_ms, int64_t* errors)
 {
     if (!sys || !lane_ms || !total_ms) return IA_ERR_INVALID_ARG;
     const void* base = scratch ? scratch : sys->d_scratch;
@@ -1497,6 +1941,7 @@ int ia_launch_phases(ia_system* sys, const void* scratch, double* lane_ms, doubl
     if (c.t_start == 0 || c.t_end < c.t_start) return IA_ERR_INVALID_ARG;
     *lane_ms = c.t_lane_end >= c.t_start ? 1e-6 * (double)(c.t_lane_end - c.t_start) : 0.0;
     *total_ms = 1e-6 * (double)(c.t_end - c.t_start);
+    if (errors) *errors = (int64_t)c.errors;
     return IA_OK;
 }
 

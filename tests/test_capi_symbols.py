@@ -53,7 +53,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(Bd.ia_system_desc) == 8 * 17 + 4 * 2 + 8
     assert ctypes.sizeof(Bd.ia_ic_soa) == 8 * 5
     assert ctypes.sizeof(Bd.ia_obs_soa) == 8 * 12
-    assert ctypes.sizeof(Bd.ia_launch_opts) == 4 * 10 + 8 * 3
+    assert ctypes.sizeof(Bd.ia_launch_opts) == 4 * 12 + 8 * 3
 
 
 def test_invalid_arguments_rejected_without_touching_gpu():

@@ -162,5 +162,6 @@ def test_launch_phases_are_ordered_and_bounded(torch_cuda):
             Bd.ia_launch(S.handle, y, p, d, out, scratch=scratch)
             e1.record()
             torch.cuda.synchronize()
-            lane_ms, total_ms = Bd.ia_launch_phases(S.handle, scratch)
+            lane_ms, total_ms, errors = Bd.ia_launch_phases(S.handle, scratch)
             assert 0.0 < lane_ms <= total_ms <= e0.elapsed_time(e1) * 1.05 + 0.1
+            assert errors == 0

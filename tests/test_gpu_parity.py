@@ -27,7 +27,10 @@ def torch_cuda():
 
 def run_gpu(descs, y0, phi0, sid, kernel, y_final=False, **kw):
     with Bd.System(descs) as S:
-        return Bd.to_numpy(S.run(y0, phi0, sid, kernel=kernel, y_final=y_final, **kw))
+        r = Bd.to_numpy(S.run(y0, phi0, sid, kernel=kernel, y_final=y_final, **kw))
+        if kernel == Bd.IA_KERNEL_PERSISTENT:
+            assert Bd.ia_launch_phases(S.handle)[2] == 0, "a bounded wait ran out"
+        return r
 
 
 @pytest.fixture(scope="module")
@@ -64,15 +67,15 @@ def test_plain_and_persistent_agree_bitwise(c1):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
 
 
-@pytest.mark.parametrize("tail_group", [6, 8])
-def test_tail_kernel_bitwise_equals_plain(c1, tail_group):
-    """Trajectories handed to the group-mode tail kernel after 300 attempted steps (nearly all of C1)
-    give the same bits as the one-thread-per-trajectory kernel: both layouts evaluate the same
-    expressions."""
+@pytest.mark.parametrize("tail_group,tail_pair,tail_sms", [(6, 0, 8), (6, 0, 64), (6, -1, 8), (8, 0, 8)])
+def test_tail_kernel_bitwise_equals_plain(c1, tail_group, tail_pair, tail_sms):
+    """Trajectories handed to the group-mode tail after 300 attempted steps (nearly all of C1) give
+    the same bits as the one-thread-per-trajectory kernel, whether a group of one warp or a pair of
+    warps (on the reserved SMs) advances them: every layout evaluates the same expressions."""
     descs, y0, phi0, sid, orc, spread = c1
     a = run_gpu(descs, y0, phi0, sid, Bd.IA_KERNEL_PLAIN, y_final=True)
     b = run_gpu(descs, y0, phi0, sid, Bd.IA_KERNEL_PERSISTENT, y_final=True, slice_budget=300,
-                tail_group=tail_group)
+                tail_group=tail_group, tail_pair=tail_pair, tail_sms=tail_sms)
     assert np.mean(a["n_steps"] + a["n_rej"] > 300) > 0.9
     for k in a:
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
@@ -125,8 +128,9 @@ def test_queue_order_and_noncooperative_fallback(c1, torch_cuda):
 
 
 def test_rcp_newton_accuracy(torch_cuda):
-    """1/r^2 by Newton-Raphson from an FP32 seed stays within 2 ulp of the correctly rounded reciprocal
-    over the whole range the integrator meets (and beyond, through its division fallback)."""
+    """1/r^2 from an FP32 seed refined by one third-order step stays within 2 ulp of the correctly
+    rounded reciprocal over the whole range the integrator meets (and beyond, through its division
+    fallback)."""
     torch = torch_cuda
     rng = np.random.default_rng(11)
     x = np.concatenate([10.0 ** rng.uniform(-40, 40, 200000), [1.0, 2.0, 3.0, 1e-300, 1e300, 5000.0 ** 2]])
