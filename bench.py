@@ -38,11 +38,14 @@ GRID = 1024
 
 # FP64 floating-point operations per attempted DP5 step of the one-lane-per-trajectory arithmetic
 # (fused multiply-add = 2), counted by ncu's per-thread FP64 instruction counters (2 dfma + dmul + dadd,
-# predicated-on threads) on the plain kernel, divided by the attempted steps of that launch; the cos
-# and reciprocal instruction sequences are included. The persistent kernel runs the same arithmetic per
-# attempt in its lane phase (its tail phase spreads one trajectory over six lanes and executes more
-# FP64 instructions in total), so this is the useful work per attempt.
-FLOPS_PER_ATTEMPT = 902.0
+# predicated-on threads) on the persistent kernel's lane phase (the bulk-only profile case, where no
+# trajectory reaches the tail), divided by the attempted steps of that launch; the cos and reciprocal
+# instruction sequences are included. The tail phase spreads one trajectory over six lanes and
+# executes more FP64 instructions in total, so this is the useful work per attempt.
+FLOPS_PER_ATTEMPT = 884.0
+# DRAM bytes per trajectory of the persistent kernel (read + write, ncu dram__bytes on the 512 x 512
+# bulk-only profile case: 34.0 MB for 262,144 trajectories): initial conditions in, observables out.
+DRAM_BYTES_PER_TRAJECTORY = 129.7
 
 
 def parse():
@@ -64,7 +67,7 @@ def parse():
     p.add_argument("--tail-group", type=int, default=0)
     p.add_argument("--tail-blocks-per-sm", type=int, default=0)
     p.add_argument("--tail-sms", type=int, default=0)
-    p.add_argument("--tail-pair", type=int, default=0, help="1/0: paired tail warps (default), -1: off")
+    p.add_argument("--tail-pair", type=int, default=0, help="1: paired tail warps on the reserved SMs; 0: off")
     p.add_argument("--diff-sample", type=int, default=4096,
                    help="trajectories of the differentiation workload timed through the tangent and adjoint "
                         "kernels (0: skip)")
@@ -379,8 +382,11 @@ def main():
     per = (outs[0]["n_steps"].to(torch.int64) + outs[0]["n_rej"].to(torch.int64)).cpu().numpy()
     max_attempts = int(max(int((o["n_steps"] + o["n_rej"]).max().item()) for o in outs))
     longest = int(np.argmax(per))
-    budget_used = args.slice_budget if args.slice_budget > 0 else 65536
+    budget_used = args.slice_budget if args.slice_budget > 0 else 131072
     long_counts = {f"over_{b}": int((per > b).sum()) for b in (budget_used, 262144, 1048576)}
+    top = np.sort(per)[::-1]
+    long_counts["top10_attempts"] = [int(v) for v in top[:10]]
+    long_counts["attempts_beyond_budget"] = int(np.maximum(per - budget_used, 0).sum())
     longest_pos = int(np.nonzero(steps[0]["order"] == longest)[0][0])
     rhs = 6 * attempts + n_local
     tmax_ms, emax_ms = total_ms, float(sum(step_ms))
@@ -446,8 +452,8 @@ def main():
                 "queue_order": "systems by sqrt(m_atom)/speed, descending",
                 "l2": "256 MiB buffer written before each step (inputs < L2)",
                 "block": args.block or 128, "refill": args.refill or 1,
-                "slice_budget": args.slice_budget or 65536, "tail_group": args.tail_group or 6,
-                "tail_sms": args.tail_sms or 8, "tail_pair": args.tail_pair >= 0 and (args.tail_group or 6) == 6,
+                "slice_budget": args.slice_budget or 131072, "tail_group": args.tail_group or 6,
+                "tail_sms": args.tail_sms or 32, "tail_pair": args.tail_pair == 1 and (args.tail_group or 6) == 6,
             },
             "rhs_evals_per_s": rhs_all / (tmax_ms / 1e3),
             "attempted_steps_per_trajectory": att_all / n_all,
@@ -455,7 +461,10 @@ def main():
             "longest_trajectory_queue_position": longest_pos / steps[0]["n"],
             "long_trajectories_step0": long_counts,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_flops / 1e12,
-                         "unit": "TFLOP/s", "frac": achieved / peak_flops, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak_flops,
+                         "traffic": DRAM_BYTES_PER_TRAJECTORY * n_local / args.steps,
+                         "traffic_note": "bytes per launch, ncu DRAM bytes of the 512x512 profile case scaled by "
+                                         "trajectories (traffic grows with them: ICs in, observables out)",
                          "peak_source": "FP64 FMA microbenchmark (ia_fp64_peak) measured in this run",
                          "flops_per_attempted_step": FLOPS_PER_ATTEMPT},
             "plain": plain,

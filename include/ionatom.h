@@ -116,14 +116,15 @@ typedef struct ia_launch_opts {
     int32_t regs_variant;       /* persistent: 1 = no register cap (default, 0 means 1); 3 = build capped
                                    for 3 resident 128-thread blocks per SM (block must be 128) */
     int32_t slice_budget;       /* persistent: attempted steps after which a trajectory is handed to the
-                                   group-mode tail kernel; 0 = 65536; -1 = never (no tail kernel) */
+                                   group-mode tail; 0 = 131072; -1 = never (no tail) */
     int32_t tail_group;         /* lanes per trajectory in the tail kernel: 6 or 8; 0 = 6 */
     int32_t tail_blocks_per_sm; /* blocks (128 threads) per SM of the clean-up tail kernel, 1..16; 0 = 1 */
     int32_t tail_sms;           /* persistent: SMs whose single block works on suspended trajectories from
-                                   the start, 1..192; 0 = 8; -1 = none */
-    int32_t tail_pair;          /* persistent, tail_group 6: on the reserved SMs, two warps on two sub-
-                                   partitions advance the same trajectories together (about twice the
-                                   step rate of one warp; bit-identical results): 0 or 1 = on, -1 = off */
+                                   the start, 1..192 (at most half the SMs are used); 0 = 32; -1 = none */
+    int32_t tail_pair;          /* persistent, tail_group 6: 1 = on the reserved SMs, two warps on two sub-
+                                   partitions advance the same trajectories together (a single long
+                                   trajectory steps 1.3x faster, but each SM holds half as many;
+                                   bit-identical results); 0 or -1 = off (default) */
     int32_t reserved;           /* must be 0 */
     int64_t suspend_capacity;   /* suspend records; 0 = min(n, max(4096, n/32)). A trajectory that finds
                                    no free record is finished by its lane. */
@@ -165,7 +166,7 @@ int ia_reserve(ia_system* sys, int64_t n, const ia_launch_opts* opts);
  * n = 0 is a no-op. opts may be NULL (defaults).
  * Persistent launches: a trajectory that has used opts->slice_budget attempted steps is saved to a
  * suspend record and finished by tail workers that give each such trajectory a group of lanes, which
- * run its steps ~2.5x faster; tail workers start at once on opts->tail_sms SMs and every other warp
+ * run its steps ~2.2x faster; tail workers start at once on opts->tail_sms SMs and every other warp
  * joins them once the queue is drained (one cooperative launch, every wait bounded). Results are
  * bit-identical to the plain kernel.
  * Concurrency: persistent launches that share the system's own scratch must not overlap; pass a

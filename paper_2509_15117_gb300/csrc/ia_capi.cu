@@ -1298,8 +1298,8 @@ struct Resolved {
     size_t bytes;   // scratch bytes
 };
 
-constexpr int DEFAULT_BUDGET = 65536;
-constexpr int DEFAULT_TAIL_SMS = 8;
+constexpr int DEFAULT_BUDGET = 131072;
+constexpr int DEFAULT_TAIL_SMS = 32;
 
 int resolve(int64_t n, const ia_launch_opts* opts, Resolved& r)
 {
@@ -1527,7 +1527,7 @@ int ia_launch(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* 
     int refill = o.refill;
     int n_sys = sys->n_sys;
     const SysDev* tab = sys->d_tab;
-    int pair = (o.tail_group != 8 && o.tail_pair >= 0) ? 1 : 0;
+    int pair = (o.tail_group != 8 && o.tail_pair == 1) ? 1 : 0;
     void* args[] = {(void*)&tab, (void*)&n_sys, (void*)&icp, (void*)&op, (void*)&nn, (void*)&ctr, (void*)&ready,
                     (void*)&susp, (void*)&cap, (void*)&refill, (void*)&budget, (void*)&tail_sms, (void*)&wait_ok,
                     (void*)&pair};

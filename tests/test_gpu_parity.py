@@ -67,7 +67,7 @@ def test_plain_and_persistent_agree_bitwise(c1):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
 
 
-@pytest.mark.parametrize("tail_group,tail_pair,tail_sms", [(6, 0, 8), (6, 0, 64), (6, -1, 8), (8, 0, 8)])
+@pytest.mark.parametrize("tail_group,tail_pair,tail_sms", [(6, 1, 8), (6, 1, 64), (6, 0, 8), (8, 0, 8)])
 def test_tail_kernel_bitwise_equals_plain(c1, tail_group, tail_pair, tail_sms):
     """Trajectories handed to the group-mode tail after 300 attempted steps (nearly all of C1) give
     the same bits as the one-thread-per-trajectory kernel, whether a group of one warp or a pair of
