@@ -71,6 +71,11 @@ def parse():
     p.add_argument("--diff-sample", type=int, default=4096,
                    help="trajectories of the differentiation workload timed through the tangent and adjoint "
                         "kernels (0: skip)")
+    p.add_argument("--workload", default="sweep", choices=["sweep", "thermal", "mixed-graph", "ftle"],
+                   help="sweep: the species x energy step (the bench line); thermal: the Monte Carlo bath; "
+                        "mixed-graph: the 250-cell parameter sweep replayed as one CUDA graph with statistics; "
+                        "ftle: the tangent kernel on the FTLE grid")
+    p.add_argument("--scale", type=float, default=0.0, help="size factor of the secondary workloads")
     p.add_argument("--profile-case", action="store_true",
                    help="run the persistent and plain kernels once on a small batch (for ncu) and exit")
     p.add_argument("--profile-grid", type=int, default=64,
@@ -150,6 +155,92 @@ def diff_bench(n: int, flush):
     adj = dict(base, value=n / (res["adjoint"][0] / 1e3), ms=res["adjoint"][0], objectives=4, seeds=4,
                checkpoint_every=10000, cost_vs_primal=res["adjoint"][0] / res["primal"][0])
     return tan, adj
+
+
+def secondary(args):
+    """One timed launch of a secondary workload after W warm-up launches on its first 2048 trajectories;
+    prints one JSON line (trajectories/s, device-timed, inputs resident)."""
+    import torch
+    from paper_2509_15117_gb300 import binding as Bd
+    from paper_2509_15117_gb300 import schedule as Sch
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    extra = {}
+    if args.workload == "thermal":
+        n_per = int(args.scale * 1e7) if args.scale > 0 else 1 << 20
+        systems, y0, phi0, sid = I.c3_workload(n_per)
+        desc = (f"Yb+-Rb Monte Carlo bath, disk sampler b_max 2000 a0, T = 10 uK, 100 uK, 1 mK, {n_per} "
+                f"trajectories each (seeds 3001-3003), random rf phase, ion at 10 uK with micromotion")
+    elif args.workload == "mixed-graph":
+        scale = args.scale if args.scale > 0 else 0.25
+        systems, y0, phi0, sid = I.c4_workload(scale=scale)
+        desc = (f"250 cells D_e x q x a x species, 4096..262144 trajectories per cell x {scale}, head-on at "
+                f"1.5 uK, random rf phase; launch + per-cell statistics replayed as one CUDA graph")
+    else:
+        sysd, y0, phi0, seeds = I.c5_ftle_grid(int(args.scale) if args.scale > 0 else 256)
+        systems, sid = [sysd], np.zeros(len(phi0), dtype=np.int32)
+        desc = (f"tangent kernel (1 direction + FTLE) on the {int(round(len(phi0) ** 0.5))}^2 cell-centred "
+                f"octant grid, Yb+-Rb head-on 1.5 uK, rf phase 0")
+    descs = [s_.as_dict() for s_ in systems]
+    n = len(phi0)
+    with Bd.System(descs) as S:
+        y, p, d = Bd.to_device_soa(y0, phi0, sid)
+        out = Bd.alloc_obs(n)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if args.workload == "ftle":
+            dyd = torch.from_numpy(np.ascontiguousarray(np.transpose(seeds, (1, 2, 0)))).cuda()
+            tan = Bd.alloc_tangent(n, 1)
+            for _ in range(args.warmup):
+                m = min(n, 2048)
+                Bd.ia_launch_tangent(S.handle, y[:, :m].contiguous(), p[:m].contiguous(), None,
+                                     Bd.alloc_obs(m), dyd[:, :, :m].contiguous(), np.zeros((1, 3)), Bd.alloc_tangent(m, 1))
+            torch.cuda.synchronize()
+            flush.zero_()
+            e0.record(stream)
+            Bd.ia_launch_tangent(S.handle, y, p, None, out, dyd, np.zeros((1, 3)), tan)
+            e1.record(stream)
+            launches = 1
+        else:
+            # queue order: slow and heavy systems first (the velocity tolerance is 1e-10 x the speed scale)
+            speeds = [s_.atol_vel / 1e-10 for s_ in systems]
+            order = torch.from_numpy(Sch.order_by_cost(sid, Sch.system_cost(systems, speeds))).cuda()
+            for _ in range(args.warmup):
+                m = min(n, 2048)
+                Bd.ia_launch(S.handle, y[:, :m].contiguous(), p[:m].contiguous(), d[:m].contiguous(), Bd.alloc_obs(m))
+            torch.cuda.synchronize()
+            if args.workload == "mixed-graph":
+                st = Bd.alloc_stats(len(descs))
+                gstream = torch.cuda.Stream()
+                with torch.cuda.stream(gstream):
+                    G = Bd.Graph(S.handle, y, p, d, out, gstream, order=order, cell_id=d, n_cells=len(descs), stats=st)
+                gstream.synchronize()
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0.record(gstream)
+                G.launch(gstream)
+                e1.record(gstream)
+                gstream.synchronize()
+                stats = Bd.stats_to_numpy(st)
+                extra["cells"] = len(descs)
+                extra["p_complex_range"] = [float((stats["n_complex"] / np.maximum(stats["n"], 1)).min()),
+                                            float((stats["n_complex"] / np.maximum(stats["n"], 1)).max())]
+                G.close()
+                launches = 4  # persistent kernel, clean-up kernel, two statistics passes
+            else:
+                flush.zero_()
+                e0.record(stream)
+                Bd.ia_launch(S.handle, y, p, d, out, order=order)
+                e1.record(stream)
+                launches = 2
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        att = int((out["n_steps"].to(torch.int64) + out["n_rej"].to(torch.int64)).sum().item())
+        mx = int((out["n_steps"] + out["n_rej"]).max().item())
+    print(json.dumps({"metric": METRIC, "workload": args.workload, "value": n / (ms / 1e3), "unit": UNIT,
+                      "ms": ms, "trajectories": n, "rhs_evals_per_s": (6 * att + n) / (ms / 1e3),
+                      "attempted_steps_per_trajectory": att / n, "max_attempted_steps": mx,
+                      "gpu_launches": launches, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": desc, "rtol": 1e-10}, **extra}), flush=True)
 
 
 def dist_env():
@@ -297,6 +388,9 @@ def main():
     rank, world, local = dist_env()
     if args.profile_case:
         profile_case(args.profile_grid)
+        return
+    if args.workload != "sweep" and args.impl == "ours":
+        secondary(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

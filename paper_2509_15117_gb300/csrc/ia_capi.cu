@@ -404,9 +404,8 @@ __device__ __forceinline__ void tail_phase(const SysDev* __restrict__ tab, const
 
 struct __align__(16) PairShared {
     double a[8][32];    // chain -> helper: a_l of stage l
-    double xp[8][32];   // helper -> chain: X3 (slot 3) and the partial positions of stages 4..7
+    double xp[8][32];   // helper -> chain: partial positions of stages 5..7 (slots 5..7)
     double kc[8][32];   // helper -> chain: ka_j + kq_j cos(Omega t_l + phi0) of stage l (ion lanes)
-    double w[4][32];    // helper -> chain: w42, w53, w64, w75
     double xn[32];      // chain -> helper: X7, the position at the step end
     double dn[3][32];   // chain -> helper: separation at X7
     double r2n[32];     // chain -> helper: its square
@@ -609,6 +608,21 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
         float errf;
         bool accept, finite;
         if (helper) {
+            // rf phases first: the chain warp needs the ion trap coefficient of stage 2 soonest.
+            // Lanes 0-3 form t + c_s h (s = 2..5; the products of the other layouts), lane 4 t + h.
+            const int cidx = gl.c < 4 ? gl.c : 0;
+            const double chsel = gl.c < 4 ? COEF_K[cidx] * h : h;
+            const double cl = cos(fma(P.Omega, t + chsel, S.phi0));
+            const double cs2 = shfl(cl, gl.base + 0), cs3 = shfl(cl, gl.base + 1), cs4 = shfl(cl, gl.base + 2);
+            const double cs5 = shfl(cl, gl.base + 3), cs67 = shfl(cl, gl.base + 4);
+            const double kqj = gl.comp < 3 ? P.kq[gl.comp] : 0.0;
+            const double kaj = gl.comp < 3 ? P.ka[gl.comp] : 0.0;
+            sh->kc[2][lane] = fma(kqj, cs2, kaj);
+            sh->kc[3][lane] = fma(kqj, cs3, kaj);
+            sh->kc[4][lane] = fma(kqj, cs4, kaj);
+            sh->kc[5][lane] = fma(kqj, cs5, kaj);
+            sh->kc[6][lane] = fma(kqj, cs67, kaj);
+            pair_post(sh->seq_h, nh);                                     // H1: trap coefficients
             Coef K;
             K.h2 = h * h;
             double cv[R];
@@ -622,24 +636,6 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
 #pragma unroll
                 for (int k = 0; k < N_COEF; ++k) kp[k] = shfl(cv[k / G], gl.base + (k % G));
             }
-            const double chsel = gl.c < 4 ? cv[0] : h;
-            const double cl = cos(fma(P.Omega, t + chsel, S.phi0));
-            const double cs2 = shfl(cl, gl.base + 0), cs3 = shfl(cl, gl.base + 1), cs4 = shfl(cl, gl.base + 2);
-            const double cs5 = shfl(cl, gl.base + 3), cs67 = shfl(cl, gl.base + 4);
-            const double kqj = gl.comp < 3 ? P.kq[gl.comp] : 0.0;
-            const double kaj = gl.comp < 3 ? P.ka[gl.comp] : 0.0;
-            sh->kc[2][lane] = fma(kqj, cs2, kaj);
-            sh->kc[3][lane] = fma(kqj, cs3, kaj);
-            sh->kc[4][lane] = fma(kqj, cs4, kaj);
-            sh->kc[5][lane] = fma(kqj, cs5, kaj);
-            sh->kc[6][lane] = fma(kqj, cs67, kaj);
-            sh->w[0][lane] = K.w42;
-            sh->w[1][lane] = K.w53;
-            sh->w[2][lane] = K.w64;
-            sh->w[3][lane] = K.w75;
-            sh->xp[3][lane] = pos3(K, x, v, a1);
-            sh->xp[4][lane] = fma(K.w41, a1, fma(K.c4, v, x));
-            pair_post(sh->seq_h, nh);                                     // H1
             double p5 = fma(K.w51, a1, fma(K.c5, v, x));
             double p6 = fma(K.w61, a1, fma(h, v, x));
             double p7 = fma(K.w71, a1, fma(h, v, x));
@@ -649,13 +645,13 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
             const double a2 = sh->a[2][lane];
             p5 = fma(K.w52, a2, p5);
             sh->xp[5][lane] = p5;
-            pair_post(sh->seq_h, nh);                                     // H2
+            pair_post(sh->seq_h, nh);                                     // H2: stage 5 partial position
             p6 = fma(K.w62, a2, p6);
             ok = pair_wait(sh->seq_c, nc) && ok;                          // C2: a3
             a3 = sh->a[3][lane];
             p6 = fma(K.w63, a3, p6);
             sh->xp[6][lane] = p6;
-            pair_post(sh->seq_h, nh);                                     // H3
+            pair_post(sh->seq_h, nh);                                     // H3: stage 6 partial position
             p7 = fma(K.w73, a3, p7);
             vacc = fma(K.b3, a3, vacc);
             ex = fma(K.f3, a3, ex);
@@ -664,29 +660,31 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
             a4 = sh->a[4][lane];
             p7 = fma(K.w74, a4, p7);
             sh->xp[7][lane] = p7;
-            pair_post(sh->seq_h, nh);                                     // H4
+            pair_post(sh->seq_h, nh);                                     // H4: step-end partial position
             vacc = fma(K.b4, a4, vacc);
             ex = fma(K.f4, a4, ex);
             ev = fma(K.e4, a4, ev);
-            ok = pair_wait(sh->seq_c, nc) && ok;                          // C4: a5
+            ok = pair_wait(sh->seq_c, nc) && ok;                          // C4: a5, a6 and the step-end position
             a5 = sh->a[5][lane];
+            a6 = sh->a[6][lane];
+            xn = sh->xn[lane];
             vacc = fma(K.b5, a5, vacc);
             ex = fma(K.f5, a5, ex);
             ev = fma(K.e5, a5, ev);
-            ok = pair_wait(sh->seq_c, nc) && ok;                          // C5: a6
-            a6 = sh->a[6][lane];
             vn = fma(K.b6, a6, vacc);
             ex = fma(K.f6, a6, ex);
             ev = fma(K.e6, a6, ev);
-            ok = pair_wait(sh->seq_c, nc) && ok;                          // C6: a7 and the step end
+            bool okx, fx, okv, fv;
+            float rx, rv;
+            err_check(P.rtol, P.atol_pos, x, xn, ex, okx, fx, rx);      // while the chain warp forms a7
+            const int j = gl.comp < 3 ? gl.comp : gl.comp - 3;
+            const double wj = shfl(vn, gl.base + 3 + j) - shfl(vn, gl.base + j);
+            const double w0 = shfl(wj, gl.base + 0), w1 = shfl(wj, gl.base + 1), w2 = shfl(wj, gl.base + 2);
+            ok = pair_wait(sh->seq_c, nc) && ok;                          // C5: a7 and the step end
             a7 = sh->a[7][lane];
-            xn = sh->xn[lane];
             r2new = sh->r2n[lane];
             const double dn0 = sh->dn[0][lane], dn1 = sh->dn[1][lane], dn2 = sh->dn[2][lane];
             ev = fma(K.e7, a7, ev);
-            bool okx, fx, okv, fv;
-            float rx, rv;
-            err_check(P.rtol, P.atol_pos, x, xn, ex, okx, fx, rx);
             err_check(P.rtol, P.atol_vel, v, vn, ev, okv, fv, rv);
             const bool real = gl.c < 6;
             const bool okk = !real || (okx && okv);
@@ -698,59 +696,64 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
             errf = 0.0f;
 #pragma unroll
             for (int k = 0; k < 6; ++k) errf = fmaxf(errf, __shfl_sync(FULL, ratio, gl.base + k));
-            const int j = gl.comp < 3 ? gl.comp : gl.comp - 3;
-            const double wj = shfl(vn, gl.base + 3 + j) - shfl(vn, gl.base + j);
-            const double w0 = shfl(wj, gl.base + 0), w1 = shfl(wj, gl.base + 1), w2 = shfl(wj, gl.base + 2);
             rd = fma(dn0, w0, fma(dn1, w1, dn2 * w2));
             sh->vn[lane] = vn;
             sh->rd[lane] = rd;
             sh->errf[lane] = errf;
             sh->dec[lane] = (accept ? 1 : 0) | (finite ? 2 : 0);
-            pair_post(sh->seq_h, nh);                                     // H5
+            pair_post(sh->seq_h, nh);                                     // H5: the decision
             if (!ok) broken = true;
         } else {
-            // stage 2
+            // stage 2, and the step coefficients of this warp's own stage positions (the products
+            // and the positions of the other layouts, bit for bit) while the helper forms the rf phases
             const double X2 = fma(COEF_K[0] * h, v, x);
             double r2, d3[3];
             const double q2 = chain_force(P, gl, X2, r2, d3);
+            const double h2 = h * h;
+            const double X3 = fma(COEF_K[4] * h2, a1, fma(COEF_K[1] * h, v, x));     // w31, c3
+            const double p4 = fma(COEF_K[5] * h2, a1, fma(COEF_K[2] * h, v, x));     // w41, c4
+            const double w42 = COEF_K[6] * h2, w53 = COEF_K[9] * h2;
+            const double w64 = COEF_K[13] * h2, w75 = COEF_K[17] * h2;
             bool ok = pair_wait(sh->seq_h, nh);                           // H1
-            const double a2 = fma(gl.comp < 3 ? sh->kc[2][lane] : 0.0, X2, q2);
+            const bool ion = gl.comp < 3;
+            const double kc2 = ion ? sh->kc[2][lane] : 0.0, kc3 = ion ? sh->kc[3][lane] : 0.0;
+            const double kc4 = ion ? sh->kc[4][lane] : 0.0, kc5 = ion ? sh->kc[5][lane] : 0.0;
+            const double kc6 = ion ? sh->kc[6][lane] : 0.0;
+            const double a2 = fma(kc2, X2, q2);
             sh->a[2][lane] = a2;
             pair_post(sh->seq_c, nc);                                     // C1
             // stage 3
-            const double X3 = sh->xp[3][lane];
-            const double c3 = fma(gl.comp < 3 ? sh->kc[3][lane] : 0.0, X3, chain_force(P, gl, X3, r2, d3));
-            sh->a[3][lane] = c3;
+            const double b3 = fma(kc3, X3, chain_force(P, gl, X3, r2, d3));
+            sh->a[3][lane] = b3;
             pair_post(sh->seq_c, nc);                                     // C2
             // stage 4
-            const double X4 = fma(sh->w[0][lane], a2, sh->xp[4][lane]);
-            const double c4 = fma(gl.comp < 3 ? sh->kc[4][lane] : 0.0, X4, chain_force(P, gl, X4, r2, d3));
-            sh->a[4][lane] = c4;
+            const double X4 = fma(w42, a2, p4);
+            const double b4 = fma(kc4, X4, chain_force(P, gl, X4, r2, d3));
+            sh->a[4][lane] = b4;
             pair_post(sh->seq_c, nc);                                     // C3
             // stage 5
             ok = pair_wait(sh->seq_h, nh) && ok;                          // H2
-            const double X5 = fma(sh->w[1][lane], c3, sh->xp[5][lane]);
-            const double c5 = fma(gl.comp < 3 ? sh->kc[5][lane] : 0.0, X5, chain_force(P, gl, X5, r2, d3));
-            sh->a[5][lane] = c5;
-            pair_post(sh->seq_c, nc);                                     // C4
+            const double X5 = fma(w53, b3, sh->xp[5][lane]);
+            const double b5 = fma(kc5, X5, chain_force(P, gl, X5, r2, d3));
             // stage 6
             ok = pair_wait(sh->seq_h, nh) && ok;                          // H3
-            const double X6 = fma(sh->w[2][lane], c4, sh->xp[6][lane]);
-            const double c6 = fma(gl.comp < 3 ? sh->kc[6][lane] : 0.0, X6, chain_force(P, gl, X6, r2, d3));
-            sh->a[6][lane] = c6;
-            pair_post(sh->seq_c, nc);                                     // C5
+            const double X6 = fma(w64, b4, sh->xp[6][lane]);
+            const double b6 = fma(kc6, X6, chain_force(P, gl, X6, r2, d3));
             // stage 7: the step end
             ok = pair_wait(sh->seq_h, nh) && ok;                          // H4
-            xn = fma(sh->w[3][lane], c5, sh->xp[7][lane]);
-            double dn[3];
-            a7 = fma(gl.comp < 3 ? sh->kc[6][lane] : 0.0, xn, chain_force(P, gl, xn, r2new, dn));
-            sh->a[7][lane] = a7;
+            xn = fma(w75, b5, sh->xp[7][lane]);
+            sh->a[5][lane] = b5;
+            sh->a[6][lane] = b6;
             sh->xn[lane] = xn;
+            pair_post(sh->seq_c, nc);                                     // C4
+            double dn[3];
+            a7 = fma(kc6, xn, chain_force(P, gl, xn, r2new, dn));
+            sh->a[7][lane] = a7;
             sh->r2n[lane] = r2new;
             sh->dn[0][lane] = dn[0];
             sh->dn[1][lane] = dn[1];
             sh->dn[2][lane] = dn[2];
-            pair_post(sh->seq_c, nc);                                     // C6
+            pair_post(sh->seq_c, nc);                                     // C5
             ok = pair_wait(sh->seq_h, nh) && ok;                          // H5: the decision
             vn = sh->vn[lane];
             rd = sh->rd[lane];
