@@ -88,11 +88,12 @@ __global__ void __launch_bounds__(128) k_plain(const SysDev* __restrict__ tab, i
 
 // Lane phase: each lane holds one trajectory at a time; idle lanes of a warp claim queue positions
 // together with one atomic add; a trajectory that has used `budget` attempted steps is written to a
-// suspend record (published by its ready flag) and the lane takes new work.
+// suspend record (published by its ready flag) and the lane takes new work. With one_batch the warp
+// claims once (32 positions) and returns when those are finished or suspended.
 __device__ __forceinline__ void lane_phase(const SysDev* __restrict__ tab, int n_sys, const IcPtrs& ic,
                                            const ObsPtrs& out, long long n, Counters* __restrict__ ctr,
                                            unsigned* __restrict__ ready, Susp* __restrict__ susp, long long cap,
-                                           int refill, int budget)
+                                           int refill, int budget, bool one_batch = false)
 {
     const int lane = threadIdx.x & 31;
     Lane L;
@@ -108,7 +109,8 @@ __device__ __forceinline__ void lane_phase(const SysDev* __restrict__ tab, int n
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(&ctr->work, (unsigned long long)n_idle);
             base = __shfl_sync(FULL, base, 0);
-            if (base + (unsigned long long)n_idle >= (unsigned long long)n) drained = true;
+            // one_batch: a single claim of 32 positions, run to completion (a tail worker lending a hand)
+            if (one_batch || base + (unsigned long long)n_idle >= (unsigned long long)n) drained = true;
             if (my < 0) {
                 const int rank = __popc(idle & ((1u << lane) - 1u));
                 const unsigned long long pos = base + (unsigned long long)rank;
@@ -173,11 +175,15 @@ __device__ __forceinline__ bool claim_record(Counters* ctr, long long cap, unsig
 // wait_ok: records may still be written by warps in the lane phase (all blocks co-resident,
 // cooperative launch), so an idle group waits for them, boundedly; otherwise an idle group stops
 // as soon as nothing is left to claim.
+// help_n > 0: a worker with no trajectory and no record to take returns 1 while positions of the
+// lane-phase queue (of length help_n) are left, so that its caller can run a batch of the lane phase
+// (the reserved SMs then add to the bulk whenever the tail queue is empty); otherwise returns 0 when
+// the tail is done.
 template <int G>
-__device__ __forceinline__ void tail_phase(const SysDev* __restrict__ tab, const IcPtrs& ic, const ObsPtrs& out,
-                                           const Susp* __restrict__ susp, const unsigned* __restrict__ ready,
-                                           Counters* __restrict__ ctr, long long cap, bool wait_ok,
-                                           unsigned long long total_warps)
+__device__ __forceinline__ int tail_phase(const SysDev* __restrict__ tab, const IcPtrs& ic, const ObsPtrs& out,
+                                          const Susp* __restrict__ susp, const unsigned* __restrict__ ready,
+                                          Counters* __restrict__ ctr, long long cap, bool wait_ok,
+                                          unsigned long long total_warps, long long help_n = 0)
 {
     constexpr int R = (N_COEF + G - 1) / G;  // coefficient rounds per lane
     const GroupLane<G> gl = group_lane<G>();
@@ -264,6 +270,7 @@ __device__ __forceinline__ void tail_phase(const SysDev* __restrict__ tab, const
         }
         if (!__any_sync(FULL, active)) {
             if (__all_sync(FULL, drained)) break;
+            if (help_n > 0 && *(volatile unsigned long long*)&ctr->work < (unsigned long long)help_n) return 1;
             // nothing to run yet: wait for the lane phase to publish records
             if (++idle_spins > IDLE_SPIN_LIMIT) {
                 if ((threadIdx.x & 31) == 0) atomicAdd(&ctr->errors, 1ull);
@@ -386,6 +393,7 @@ __device__ __forceinline__ void tail_phase(const SysDev* __restrict__ tab, const
             }
         }
     }
+    return 0;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -862,7 +870,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sched(const SysDev* __restrict_
         tail_phase_pair(tab, ic, out, susp, ready, ctr, cap, total_warps, &pair_sh[G == 6 ? (w >> 1) : 0],
                         (w & 1) != 0);
     } else if (r != 2 && budget > 0) {
-        tail_phase<G>(tab, ic, out, susp, ready, ctr, cap, wait_ok != 0, total_warps);
+        // a reserved-SM worker that finds the tail queue empty runs batches of the lane phase meanwhile
+        const long long help_n = r == 1 ? n : 0;
+        while (tail_phase<G>(tab, ic, out, susp, ready, ctr, cap, wait_ok != 0, total_warps, help_n) == 1)
+            lane_phase(tab, n_sys, ic, out, n, ctr, ready, susp, cap, refill, budget, true);
     }
     if ((threadIdx.x & 31) == 0) atomicMax(&ctr->t_end, global_ns());
 }
