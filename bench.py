@@ -44,8 +44,8 @@ GRID = 1024
 # executes more FP64 instructions in total, so this is the useful work per attempt.
 FLOPS_PER_ATTEMPT = 884.0
 # DRAM bytes per trajectory of the persistent kernel (read + write, ncu dram__bytes on the 512 x 512
-# bulk-only profile case: 34.0 MB for 262,144 trajectories): initial conditions in, observables out.
-DRAM_BYTES_PER_TRAJECTORY = 129.7
+# bulk-only profile case: 38.8 MB for 262,144 trajectories): initial conditions in, observables out.
+DRAM_BYTES_PER_TRAJECTORY = 148.0
 
 
 def parse():
@@ -250,12 +250,29 @@ def dist_env():
     return rank, world, local
 
 
+def step_offset(step: int, stride: int, rank: int = 0, world: int = 1) -> int:
+    """Grid offset of a (step, rank) pair: consecutive pairs take consecutive offsets, so ranks of one
+    step integrate disjoint sub-grids whenever stride >= world (with stride 1 every rank integrates
+    the whole sweep: replicas)."""
+    return (step * world + rank) % stride
+
+
 def batch(step: int, stride: int, rank: int = 0, world: int = 1):
-    """Batch of a step: one grid offset per (step, rank) pair; disjoint across ranks."""
-    k = step * world + rank
-    off = k % stride
+    """Batch of a step (see step_offset)."""
+    off = step_offset(step, stride, rank, world)
     systems, y0, phi0, sid = I.c2_workload(n_grid=GRID, stride=stride, offset=off)
     return systems, y0, phi0, sid
+
+
+def reduce_over_ranks(dist, device, maxima, sums):
+    """Whole-job figures of a multi-rank run: the maximum over ranks of each entry of `maxima` (step
+    times) and the sum of each entry of `sums` (trajectories, RHS evaluations, attempts)."""
+    import torch
+    t = torch.tensor(maxima, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor(sums, dtype=torch.float64, device=device)
+    dist.all_reduce(c)
+    return [float(x) for x in t.tolist()], [float(x) for x in c.tolist()]
 
 
 class ClockSampler:
@@ -485,12 +502,8 @@ def main():
     rhs = 6 * attempts + n_local
     tmax_ms, emax_ms = total_ms, float(sum(step_ms))
     if dist is not None:
-        t = torch.tensor([total_ms, emax_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax_ms, emax_ms = (float(x) for x in t.tolist())
-        c = torch.tensor([float(n_local), float(rhs), float(attempts)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(c)
-        n_all, rhs_all, att_all = (float(x) for x in c.tolist())
+        (tmax_ms, emax_ms), (n_all, rhs_all, att_all) = reduce_over_ranks(
+            dist, "cuda", [total_ms, emax_ms], [float(n_local), float(rhs), float(attempts)])
     else:
         n_all, rhs_all, att_all = float(n_local), float(rhs), float(attempts)
     value = n_all / (tmax_ms / 1e3)
