@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ia_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "ia_sample_oracle.c")]
 _LIB = os.path.join(_HERE, "libia_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -62,6 +63,20 @@ class OrcResult(ctypes.Structure):
     ]
 
 
+class OrcSampler(ctypes.Structure):
+    """Counter-based initial-condition sampler (``ia_sample_oracle.c``)."""
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("random_phase", ctypes.c_int32),
+        ("micromotion", ctypes.c_int32), ("rf_sign", ctypes.c_int32),
+        ("m_ion", ctypes.c_double), ("m_atom", ctypes.c_double), ("Omega", ctypes.c_double),
+        ("q", ctypes.c_double * 3), ("r0", ctypes.c_double), ("E", ctypes.c_double),
+        ("kT", ctypes.c_double), ("kT_ion", ctypes.c_double), ("b_max", ctypes.c_double),
+        ("phase", ctypes.c_double), ("seed", ctypes.c_uint64),
+    ]
+
+
+SAMPLE_HEAD_ON, SAMPLE_SPHERE, SAMPLE_DISK = 0, 1, 2
+
 RESULT_DTYPE = np.dtype([
     ("theta_s", "<f8"), ("dp", "<f8"), ("dE_ion", "<f8"), ("t_final", "<f8"),
     ("t_first_bounce", "<f8"), ("t_last_bounce", "<f8"), ("y_final", "<f8", (12,)),
@@ -73,10 +88,10 @@ assert RESULT_DTYPE.itemsize == ctypes.sizeof(OrcResult)
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc into ``oracle/libia_oracle.so`` (in-tree, git-ignored)."""
     with _lock:
-        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        if not force and os.path.exists(_LIB) and all(os.path.getmtime(_LIB) >= os.path.getmtime(p) for p in _SRCS):
             return _LIB
         tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"]
+        cmd = ["gcc", *CFLAGS, "-o", tmp, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
         return _LIB
@@ -103,6 +118,11 @@ def lib():
         L.orc_ionatom_fixed.argtypes = [P(OrcSystem), d, d, d, ctypes.c_int64, dp]
         L.orc_ionatom_segment.argtypes = [P(OrcSystem), d, d, d, dp, P(ctypes.c_int64), P(ctypes.c_int64)]
         L.orc_max_threads.restype = ctypes.c_int32
+        u64 = ctypes.c_uint64
+        L.orc_philox4x64.argtypes = [P(u64), P(u64), P(u64)]
+        L.orc_philox4x64_stream.argtypes = [u64, u64, u64, ctypes.c_int64, ctypes.c_int64, P(u64)]
+        L.orc_sample_ics.argtypes = [P(OrcSampler), ctypes.c_int64, ctypes.c_int64, dp, dp]
+        L.orc_sample_ics.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -305,3 +325,50 @@ def gradient(desc: dict, y0, phi0: float, hs, mode: int):
         cols.append(out)
     J = np.vstack(cols)  # (15, 4): row = direction, column = objective
     return np.ascontiguousarray(J[:12].T), np.ascontiguousarray(J[12:].T)
+
+
+def philox4x64(ctr, key) -> np.ndarray:
+    """One Philox4x64-10 block of counter ctr (4 words) under key (2 words)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    P = ctypes.POINTER(ctypes.c_uint64)
+    lib().orc_philox4x64(c.ctypes.data_as(P), k.ctypes.data_as(P), out.ctypes.data_as(P))
+    return out
+
+
+def philox4x64_stream(key0: int, key1: int, ctr1: int, first: int, n: int) -> np.ndarray:
+    """n blocks, block j of counter (first + j, ctr1, 0, 0); returns (n, 4) uint64."""
+    out = np.zeros((n, 4), dtype=np.uint64)
+    lib().orc_philox4x64_stream(key0, key1, ctr1, first, n, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    return out
+
+
+def make_sampler(kind: int, desc: dict, seed: int, E: float = 0.0, kT: float = 0.0, kT_ion: float = 0.0,
+                 b_max: float = 0.0, random_phase: bool = True, phase: float = 0.0,
+                 micromotion: bool = False) -> OrcSampler:
+    """Sampler struct; the masses, Omega, q, r0 and rf sign come from a descriptor dict."""
+    s = OrcSampler()
+    s.kind = kind
+    s.random_phase = int(bool(random_phase))
+    s.micromotion = int(bool(micromotion))
+    s.rf_sign = int(desc.get("rf_sign", 1))
+    s.m_ion = desc["m_ion"]
+    s.m_atom = desc["m_atom"]
+    s.Omega = desc["Omega"]
+    for j in range(3):
+        s.q[j] = desc["q"][j]
+    s.r0 = desc["r0"]
+    s.E, s.kT, s.kT_ion, s.b_max, s.phase = E, kT, kT_ion, b_max, phase
+    s.seed = seed
+    return s
+
+
+def sample_ics(sampler: OrcSampler, first: int, n: int):
+    """Initial states of trajectories first .. first + n - 1: (y0 (n, 12), phi0 (n,))."""
+    y = np.zeros((n, 12))
+    ph = np.zeros(n)
+    rc = lib().orc_sample_ics(ctypes.byref(sampler), first, n, _dptr(y), _dptr(ph))
+    if rc != 0:
+        raise ValueError("sampler parameters out of range")
+    return y, ph
