@@ -71,11 +71,17 @@ def parse():
     p.add_argument("--diff-sample", type=int, default=4096,
                    help="trajectories of the differentiation workload timed through the tangent and adjoint "
                         "kernels (0: skip)")
-    p.add_argument("--workload", default="sweep", choices=["sweep", "thermal", "mixed-graph", "ftle"],
+    p.add_argument("--workload", default="sweep",
+                   choices=["sweep", "thermal", "mixed-graph", "ftle", "sampler", "energy-scan"],
                    help="sweep: the species x energy step (the bench line); thermal: the Monte Carlo bath; "
                         "mixed-graph: the 250-cell parameter sweep replayed as one CUDA graph with statistics; "
-                        "ftle: the tangent kernel on the FTLE grid")
+                        "ftle: the tangent kernel on the FTLE grid; sampler: initial conditions drawn on the "
+                        "device; energy-scan: the collision-energy scan with device-drawn initial conditions, "
+                        "per-cell statistics and the threshold fit")
     p.add_argument("--scale", type=float, default=0.0, help="size factor of the secondary workloads")
+    p.add_argument("--sampler-sample", type=int, default=1 << 24,
+                   help="trajectories whose initial conditions are drawn on the device, per sampler kind, "
+                        "in a timed side measurement (0: skip)")
     p.add_argument("--profile-case", action="store_true",
                    help="run the persistent and plain kernels once on a small batch (for ncu) and exit")
     p.add_argument("--profile-grid", type=int, default=64,
@@ -163,8 +169,16 @@ def secondary(args):
     import torch
     from paper_2509_15117_gb300 import binding as Bd
     from paper_2509_15117_gb300 import schedule as Sch
+    if args.workload == "energy-scan":
+        energy_scan(args)
+        return
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    if args.workload == "sampler":
+        n = int(args.scale * (1 << 20)) if args.scale > 0 else 1 << 24
+        print(json.dumps({"workload": "sampler", "ic_sampler": sampler_bench(n, flush), "dtype": "f64",
+                          "data": "synthetic"}), flush=True)
+        return
     extra = {}
     if args.workload == "thermal":
         n_per = int(args.scale * 1e7) if args.scale > 0 else 1 << 20
@@ -241,6 +255,133 @@ def secondary(args):
                       "attempted_steps_per_trajectory": att / n, "max_attempted_steps": mx,
                       "gpu_launches": launches, "dtype": "f64", "data": "synthetic",
                       "config": {"workload": desc, "rtol": 1e-10}, **extra}), flush=True)
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this GPU type (generated file), else the earlier measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+IC_BYTES = 13 * 8  # y0 (12 doubles) and phi0 written per trajectory
+
+
+def sampler_bench(n: int, flush, seed: int = 7):
+    """ia_sample_ics for each kind on n trajectories (a warm-up launch, then one launch timed with CUDA
+    events after an L2 flush), against the pinned host-to-device copy of the same bytes."""
+    import torch
+    from paper_2509_15117_gb300 import binding as Bd
+    stream = torch.cuda.current_stream()
+    d = I.make_system("Rb").as_dict()
+    kinds = {"head_on": (Bd.IA_SAMPLE_HEAD_ON, dict(E=I.kelvin(1.5e-6))),
+             "sphere": (Bd.IA_SAMPLE_SPHERE, dict(kT=I.kelvin(1e-4), kT_ion=I.kelvin(1e-5))),
+             "disk": (Bd.IA_SAMPLE_DISK, dict(kT=I.kelvin(1e-3), kT_ion=I.kelvin(1e-5), b_max=2000.0,
+                                              micromotion=True))}
+    y = torch.empty((12, n), dtype=torch.float64, device="cuda")
+    ph = torch.empty((n,), dtype=torch.float64, device="cuda")
+    peak, src = hbm_peak_gbs()
+    res = {}
+    for name, (kind, kw) in kinds.items():
+        smp = Bd.make_sampler(kind, d, seed, **kw)
+        Bd.ia_sample_ics(smp, 0, y, ph)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0.record(stream)
+        Bd.ia_sample_ics(smp, 0, y, ph)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        gbs = n * IC_BYTES / (ms / 1e3) / 1e9
+        res[name] = {"ms": ms, "value": n / (ms / 1e3), "unit": "initial conditions/s", "write_GBps": gbs,
+                     "write_frac_of_hbm": gbs / peak}
+    host = torch.empty((13, n), dtype=torch.float64).pin_memory()
+    dev = torch.empty((13, n), dtype=torch.float64, device="cuda")
+    dev.copy_(host, non_blocking=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    dev.copy_(host, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    h2d_ms = e0.elapsed_time(e1)
+    del y, ph, host, dev
+    return {"trajectories": n, "bytes_per_trajectory": IC_BYTES, "kinds": res,
+            "h2d_copy_same_bytes_ms": h2d_ms, "hbm_peak_GBps": peak, "hbm_peak_source": src,
+            "generator": "Philox4x64-10, 4 blocks per thermal trajectory (1 for head-on), Box-Muller"}
+
+
+def energy_scan(args):
+    """Fig. 4 workload: device-drawn head-on initial conditions with a random rf phase for every
+    (species, energy) cell, one persistent launch over all cells, per-cell statistics; then the
+    threshold fit of P_complex(E) per species against W0^3D. Timed on the device from the first
+    sampler launch to the end of the statistics."""
+    import torch
+    from paper_2509_15117_gb300 import binding as Bd
+    from paper_2509_15117_gb300 import schedule as Sch
+    from paper_2509_15117_gb300 import statistics as St
+    scale = args.scale if args.scale > 0 else 0.1
+    n_per = max(1, int(round(scale * 10_000)))
+    systems, energies, names = I.energy_scan_systems()
+    descs = [s_.as_dict() for s_ in systems]
+    n_cells = len(descs)
+    n = n_per * n_cells
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    y = torch.empty((12, n), dtype=torch.float64, device="cuda")
+    ph = torch.empty((n,), dtype=torch.float64, device="cuda")
+    sid = torch.arange(n_cells, dtype=torch.int32, device="cuda").repeat_interleave(n_per)
+    speeds = [s_.atol_vel / 1e-10 for s_ in systems]
+    order = torch.from_numpy(Sch.order_by_cost(sid.cpu().numpy(), Sch.system_cost(systems, speeds))).cuda()
+    samplers = [Bd.make_sampler(Bd.IA_SAMPLE_HEAD_ON, descs[c], 4004, E=float(energies[c])) for c in range(n_cells)]
+    with Bd.System(descs) as S:
+        out = Bd.alloc_obs(n)
+        st = Bd.alloc_stats(n_cells)
+        Bd.ia_reserve(S.handle, n, kernel=Bd.IA_KERNEL_PERSISTENT)
+        Bd.ia_reserve_stats(S.handle, n, n_cells)
+        for _ in range(args.warmup):  # one cell's first 256 trajectories, highest energy of the first species
+            c = n_cells // len(I.C2_SPECIES) - 1
+            Bd.ia_sample_ics(samplers[c], c * n_per, y[:, :256], ph[:256])
+            Bd.ia_launch(S.handle, y[:, :256], ph[:256], torch.full((256,), c, dtype=torch.int32, device="cuda"),
+                         Bd.alloc_obs(256))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        for c in range(n_cells):
+            a = c * n_per
+            Bd.ia_sample_ics(samplers[c], a, y[:, a:a + n_per], ph[a:a + n_per])
+        Bd.ia_launch(S.handle, y, ph, sid, out, order=order)
+        Bd.ia_reduce_stats(S.handle, out, n, sid, n_cells, st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        waits = Bd.ia_launch_phases(S.handle)[2]
+        stats = Bd.stats_to_numpy(st)
+        att = int((out["n_steps"].to(torch.int64) + out["n_rej"].to(torch.int64)).sum().item())
+        mx = int((out["n_steps"] + out["n_rej"]).max().item())
+    per_species = {}
+    for sp in dict.fromkeys(names):
+        cells = [c for c in range(n_cells) if names[c] == sp]
+        E = energies[cells]
+        k = stats["n_complex"][cells]
+        m = stats["n"][cells]
+        fit = St.fit_threshold(E, k, m)
+        d0 = systems[cells[0]]
+        w0 = St.w0_3d(d0.m_atom, d0.m_ion, d0.Omega, d0.a[0], d0.q[0], 0.5 * d0.alpha)
+        per_species[sp] = {"E_threshold_uK": fit["E_th"] / I.K_TO_HARTREE * 1e6, "W0_3D_uK": w0 / I.K_TO_HARTREE * 1e6,
+                           "threshold_over_W0": fit["E_th"] / w0, "P0": fit["P0"], "width_ln_E": fit["width_ln"],
+                           "P_complex_lowest_E": float(k[0] / m[0]), "P_complex_highest_E": float(k[-1] / m[-1])}
+    desc = (f"collision-energy scan: Yb+ head-on with {', '.join(dict.fromkeys(names))}, "
+            f"{n_cells // len(per_species)} energies 30 nK..1 mK, {n_per} trajectories per energy, r0 = 20,000 a0, "
+            f"D_e = 1 K, q = 0.1, t_max = 3 ms, random rf phase; initial conditions drawn on the device")
+    print(json.dumps({"metric": METRIC, "workload": "energy-scan", "value": n / (ms / 1e3), "unit": UNIT, "ms": ms,
+                      "trajectories": n, "attempted_steps_per_trajectory": att / n, "max_attempted_steps": mx,
+                      "wait_errors": waits, "gpu_launches": n_cells + 4, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": desc, "rtol": 1e-10}, "per_species": per_species}), flush=True)
 
 
 def dist_env():
@@ -542,6 +683,10 @@ def main():
     if rank == 0 and args.diff_sample > 0:
         diff = diff_bench(args.diff_sample, flush)
 
+    sampler = None
+    if rank == 0 and args.sampler_sample > 0:
+        sampler = sampler_bench(args.sampler_sample, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -588,6 +733,8 @@ def main():
         }
         if diff is not None:
             line["tangent"], line["adjoint"] = diff
+        if sampler is not None:
+            line["ic_sampler"] = sampler
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

@@ -378,6 +378,72 @@ int ia_launch_adjoint(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_o
                       const ia_tangent_in* seeds, const ia_adjoint_out* aout, const ia_adjoint_opts* opts,
                       void* stream);
 
+/* ---- initial conditions drawn on the device ---- */
+
+#define IA_SAMPLE_HEAD_ON 0  /* head-on runs: ion at rest at the centre; atom at r0 x_hat moving at -v0 x_hat,
+                                E = m_a v0^2 / 2, x_hat uniform on the octant's surface (cos theta = u1,
+                                phi = (pi/2) u2) */
+#define IA_SAMPLE_SPHERE 1   /* thermal runs as the paper draws them: atom uniform on the r0 sphere
+                                (cos theta = 2 u1 - 1, phi = 2 pi u2), velocity components Gaussian with
+                                variance kT/m_a, the vector negated where v . x_hat >= 0; thermal ion */
+#define IA_SAMPLE_DISK 2     /* thermal runs with the impact parameter uniform over a disk: atom velocity as
+                                above; b = b_max sqrt(u1) at azimuth psi = 2 pi u2 about v_hat, measured from
+                                e1 = unit(v_hat x r) (r = z_hat if |v_hat_z| < 0.9, else x_hat) toward
+                                e2 = v_hat x e1; x_a = b (cos psi e1 + sin psi e2) - sqrt(r0^2 - b^2) v_hat;
+                                thermal ion */
+
+/* Parameters of a sampler. The masses, Omega, q, r0 and rf_sign are those of the system the
+ * trajectories will be integrated in. */
+typedef struct ia_sampler {
+    int32_t kind;          /* IA_SAMPLE_* */
+    int32_t random_phase;  /* 1: phi0 = 2 pi u0, uniform on (0, 2 pi) (Fig. 4 caption); 0: phi0 = phase */
+    int32_t micromotion;   /* thermal kinds, 0 or 1: add the ion's lowest-order micromotion at phi0,
+                              x_j = X_j (1 + s q_j/2 cos phi0), v_j = V_j (1 + s q_j/2 cos phi0)
+                              - X_j s (q_j Omega/2) sin phi0 */
+    int32_t rf_sign;       /* s: +1 or -1 */
+    double m_ion, m_atom;  /* m_e (> 0) */
+    double Omega;          /* rad per a.u. of time */
+    double q[3];           /* Mathieu q per axis */
+    double r0;             /* start sphere, a0 (> 0) */
+    double E;              /* head-on: collision energy, E_h (> 0) */
+    double kT;             /* thermal kinds: k_B T of the atom, E_h (> 0) */
+    double kT_ion;         /* thermal kinds: k_B T of the ion, E_h (>= 0; 0 = at rest at the centre). The
+                              secular position X_j and velocity V_j are Gaussian with variances
+                              kT_ion/(m_ion omega^2) and kT_ion/m_ion, omega = |q_x| Omega / 2^(3/2) (> 0
+                              when kT_ion > 0) */
+    double b_max;          /* disk: radius, a0, 0 <= b_max < r0 */
+    double phase;          /* phi0 when random_phase = 0 */
+    uint64_t seed;         /* word 0 of the generator's key (word 1 is the kind) */
+} ia_sampler;
+
+/*
+ * Raw generator (no counterpart in the paper): Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11).
+ * Block j, j = 0 .. n_blocks - 1, is the ten-round map of the counter (first + j, ctr1, 0, 0) under the
+ * key (key0, key1); its four words go to out[4j .. 4j + 3] (device array, 8-byte aligned).
+ * first >= 0 and first + n_blocks must not overflow. Asynchronous on `stream`.
+ */
+int ia_philox4x64(uint64_t key0, uint64_t key1, uint64_t ctr1, int64_t first, int64_t n_blocks, uint64_t* out,
+                  void* stream);
+
+/*
+ * Draw the initial conditions of trajectories first .. first + n - 1 on the device: y0 (12 x ld, the
+ * layout of ia_ic_soa.y0) and phi0 (n) get the state at t = 0 and the rf phase of trajectory
+ * first + i in column i. Initial conditions as the paper's runs draw them (head-on paragraph, thermal
+ * paragraph, Fig. 3 and Fig. 4 captions); see IA_SAMPLE_*.
+ * Random numbers: trajectory g uses the Philox4x64-10 blocks of the counters (g, j, 0, 0), j = 0..3,
+ * under the key (seed, kind). Word w of block j gives u[4j + w] = ((word >> 11) | 1) 2^-53, in (0, 1).
+ *   - u0 is the rf phase, u1 and u2 the direction or the disk point;
+ *   - u4 .. u13 are five Box-Muller pairs g[2p] = sqrt(-2 ln u[4+2p]) cos(2 pi u[5+2p]), g[2p+1] the sine;
+ *   - g0..g2 scale to the atom velocity, g3..g5 to the ion's secular position, g6..g8 to its secular
+ *     velocity.
+ * A trajectory's values depend only on its index, the seed and the kind: any index range can be drawn
+ * alone (in chunks, or one range per rank) and matches the whole batch. n = 0 is a no-op.
+ * IA_ERR_INVALID_ARG for a parameter out of the ranges above, or when ld < n; IA_ERR_ALIGNMENT for
+ * unaligned pointers. Asynchronous on `stream`.
+ */
+int ia_sample_ics(const ia_sampler* s, int64_t first, int64_t n, double* y0, double* phi0, int64_t ld,
+                  void* stream);
+
 /*
  * Test hook (no counterpart in the paper): y[i] = 1/x[i] computed as the integrator computes 1/r^2
  * (Newton-Raphson from an FP32 seed). x, y: device arrays of n doubles, x[i] > 0. Asynchronous.

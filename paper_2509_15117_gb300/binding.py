@@ -32,8 +32,12 @@ ST_COMPLEX = 1 << 8
 EXPORTED = ("ia_system_create", "ia_system_destroy", "ia_system_count", "ia_scratch_bytes", "ia_reserve",
             "ia_launch", "ia_launch_static", "ia_reduce_stats", "ia_reserve_stats", "ia_graph_create",
             "ia_graph_launch", "ia_graph_destroy", "ia_autotune", "ia_launch_phases", "ia_launch_tangent",
-            "ia_adjoint_scratch_bytes", "ia_launch_adjoint", "ia_fp64_peak", "ia_rcp_check", "ia_error_string",
-            "ia_version")
+            "ia_adjoint_scratch_bytes", "ia_launch_adjoint", "ia_philox4x64", "ia_sample_ics", "ia_fp64_peak",
+            "ia_rcp_check", "ia_error_string", "ia_version")
+
+IA_SAMPLE_HEAD_ON = 0
+IA_SAMPLE_SPHERE = 1
+IA_SAMPLE_DISK = 2
 
 STATS_BOUNCE_BINS = 32
 STATS_LIFETIME_BINS = 64
@@ -107,6 +111,14 @@ class ia_tangent_out(ctypes.Structure):
                 ("ld", ctypes.c_int64)]
 
 
+class ia_sampler(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("random_phase", ctypes.c_int32), ("micromotion", ctypes.c_int32),
+                ("rf_sign", ctypes.c_int32), ("m_ion", ctypes.c_double), ("m_atom", ctypes.c_double),
+                ("Omega", ctypes.c_double), ("q", ctypes.c_double * 3), ("r0", ctypes.c_double),
+                ("E", ctypes.c_double), ("kT", ctypes.c_double), ("kT_ion", ctypes.c_double),
+                ("b_max", ctypes.c_double), ("phase", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -168,6 +180,12 @@ def load(build_if_missing: bool = True):
     L.ia_reserve.restype = ctypes.c_int
     L.ia_rcp_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
     L.ia_rcp_check.restype = ctypes.c_int
+    L.ia_philox4x64.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
+                                ctypes.c_void_p, ctypes.c_void_p]
+    L.ia_philox4x64.restype = ctypes.c_int
+    L.ia_sample_ics.argtypes = [P(ia_sampler), ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_int64, ctypes.c_void_p]
+    L.ia_sample_ics.restype = ctypes.c_int
     L.ia_fp64_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, P(ctypes.c_double)]
     L.ia_fp64_peak.restype = ctypes.c_int
     L.ia_error_string.argtypes = [ctypes.c_int]
@@ -306,6 +324,42 @@ def ia_reserve(handle: int, n: int, **kw) -> None:
 
 def ia_rcp_check(x, y, stream=None) -> None:
     _check(load().ia_rcp_check(x.data_ptr(), y.data_ptr(), int(x.numel()), _stream_ptr(stream)))
+
+
+def make_sampler(kind: int, desc: dict, seed: int, E: float = 0.0, kT: float = 0.0, kT_ion: float = 0.0,
+                 b_max: float = 0.0, random_phase: bool = True, phase: float = 0.0,
+                 micromotion: bool = False) -> ia_sampler:
+    """ia_sampler for the system of a descriptor dict (masses, Omega, q, r0 and rf sign taken from it)."""
+    s = ia_sampler()
+    s.kind = int(kind)
+    s.random_phase = int(bool(random_phase))
+    s.micromotion = int(bool(micromotion))
+    s.rf_sign = int(desc.get("rf_sign", 1))
+    s.m_ion = float(desc["m_ion"])
+    s.m_atom = float(desc["m_atom"])
+    s.Omega = float(desc["Omega"])
+    for j in range(3):
+        s.q[j] = float(desc["q"][j])
+    s.r0 = float(desc["r0"])
+    s.E, s.kT, s.kT_ion, s.b_max, s.phase = float(E), float(kT), float(kT_ion), float(b_max), float(phase)
+    s.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    return s
+
+
+def ia_sample_ics(sampler: ia_sampler, first: int, y0_soa, phi0, stream=None) -> None:
+    """Fill device tensors y0_soa (12, n) float64 (row stride = ld) and phi0 (n,) with the initial
+    conditions of trajectories first .. first + n - 1."""
+    n = int(phi0.shape[0])
+    ld = int(y0_soa.stride(0)) if n > 0 else 0
+    _check(load().ia_sample_ics(ctypes.byref(sampler), int(first), n, y0_soa.data_ptr(), phi0.data_ptr(), ld,
+                                _stream_ptr(stream)))
+
+
+def ia_philox4x64(key0: int, key1: int, ctr1: int, first: int, out, stream=None) -> None:
+    """Raw Philox4x64-10 blocks into a device tensor out (n_blocks, 4) of int64 (the words' bits)."""
+    m = 0xFFFFFFFFFFFFFFFF
+    _check(load().ia_philox4x64(int(key0) & m, int(key1) & m, int(ctr1) & m, int(first), int(out.shape[0]),
+                                out.data_ptr(), _stream_ptr(stream)))
 
 
 def _ic_struct(y0_soa, phi0, sys_id, order) -> ia_ic_soa:

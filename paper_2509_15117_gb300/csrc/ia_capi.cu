@@ -15,6 +15,7 @@
 //                 the longest complex's latency, instead of their sum.
 //   k_tail<G>     finishes records the fused kernel left (normally none).
 //   k_fp64_fma    FP64 FMA throughput microbenchmark: the denominator of the integrator's roofline.
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -27,6 +28,7 @@
 #include "ia_stats.cuh"
 #include "ia_tangent.cuh"
 #include "ia_adjoint.cuh"
+#include "ia_sample.cuh"
 #include "../../include/ionatom.h"
 
 using namespace ia;
@@ -1248,6 +1250,18 @@ namespace {
 
 bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
+// SM count of the current device, which must be an sm_103 GPU.
+int sample_device(int* sms)
+{
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return IA_ERR_NO_DEVICE;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return IA_ERR_NO_DEVICE;
+    return (major == 10 && minor == 3 && *sms > 0) ? IA_OK : IA_ERR_NO_DEVICE;
+}
+
 bool valid_desc(const ia_system_desc& d)
 {
     auto pos = [](double x) { return std::isfinite(x) && x > 0.0; };
@@ -1957,6 +1971,76 @@ int ia_launch_phases(ia_system* sys, const void* scratch, double* lane_ms, doubl
     *total_ms = 1e-6 * (double)(c.t_end - c.t_start);
     if (errors) *errors = (int64_t)c.errors;
     return IA_OK;
+}
+
+int ia_philox4x64(uint64_t key0, uint64_t key1, uint64_t ctr1, int64_t first, int64_t n_blocks, uint64_t* out,
+                  void* stream)
+{
+    if (n_blocks < 0 || first < 0 || first > INT64_MAX - n_blocks) return IA_ERR_INVALID_ARG;
+    if (n_blocks == 0) return IA_OK;
+    if (!out) return IA_ERR_INVALID_ARG;
+    if (!aligned8(out)) return IA_ERR_ALIGNMENT;
+    if (n_blocks > INT64_MAX / 4) return IA_ERR_TOO_LARGE;
+    int sms = 0;
+    if (sample_device(&sms) != IA_OK) return IA_ERR_NO_DEVICE;
+    const long long grid = std::min<long long>((n_blocks + ia_sample::SAMPLE_THREADS - 1) / ia_sample::SAMPLE_THREADS,
+                                               8LL * sms);
+    ia_sample::k_philox<<<(unsigned)grid, ia_sample::SAMPLE_THREADS, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        key0, key1, ctr1, (long long)first, (long long)n_blocks, reinterpret_cast<unsigned long long*>(out));
+    return cudaGetLastError() == cudaSuccess ? IA_OK : IA_ERR_CUDA;
+}
+
+int ia_sample_ics(const ia_sampler* s, int64_t first, int64_t n, double* y0, double* phi0, int64_t ld, void* stream)
+{
+    if (!s || n < 0 || first < 0 || first > INT64_MAX - n) return IA_ERR_INVALID_ARG;
+    if (n == 0) return IA_OK;
+    if (!y0 || !phi0 || ld < n || ld > INT64_MAX / 12) return IA_ERR_INVALID_ARG;
+    if (!aligned8(y0) || !aligned8(phi0)) return IA_ERR_ALIGNMENT;
+    auto pos = [](double x) { return std::isfinite(x) && x > 0.0; };
+    if (s->kind < IA_SAMPLE_HEAD_ON || s->kind > IA_SAMPLE_DISK) return IA_ERR_INVALID_ARG;
+    if ((s->random_phase != 0 && s->random_phase != 1) || (s->micromotion != 0 && s->micromotion != 1) ||
+        (s->rf_sign != 1 && s->rf_sign != -1))
+        return IA_ERR_INVALID_ARG;
+    if (!pos(s->m_ion) || !pos(s->m_atom) || !pos(s->r0) || !std::isfinite(s->Omega) ||
+        (!s->random_phase && !std::isfinite(s->phase)))
+        return IA_ERR_INVALID_ARG;
+    for (int j = 0; j < 3; ++j)
+        if (!std::isfinite(s->q[j])) return IA_ERR_INVALID_ARG;
+    ia_sample::SampleParams p{};
+    p.kind = s->kind;
+    p.random_phase = s->random_phase;
+    p.micromotion = s->micromotion;
+    p.rf_sign = s->rf_sign;
+    p.r0 = s->r0;
+    p.phase = s->random_phase ? 0.0 : s->phase;
+    p.Omega = s->Omega;
+    for (int j = 0; j < 3; ++j) p.q[j] = s->q[j];
+    if (s->kind == IA_SAMPLE_HEAD_ON) {
+        if (!pos(s->E)) return IA_ERR_INVALID_ARG;
+        p.v0 = std::sqrt(2.0 * s->E / s->m_atom);
+    } else {
+        if (!pos(s->kT) || !std::isfinite(s->kT_ion) || s->kT_ion < 0.0) return IA_ERR_INVALID_ARG;
+        const double omega = std::fabs(s->q[0]) * s->Omega / (2.0 * std::sqrt(2.0));
+        if (s->kT_ion > 0.0 && !pos(omega)) return IA_ERR_INVALID_ARG;
+        if (s->kind == IA_SAMPLE_DISK && !(std::isfinite(s->b_max) && s->b_max >= 0.0 && s->b_max < s->r0))
+            return IA_ERR_INVALID_ARG;
+        p.sig_a = std::sqrt(s->kT / s->m_atom);
+        p.sig_v = std::sqrt(s->kT_ion / s->m_ion);
+        p.sig_x = s->kT_ion > 0.0 ? p.sig_v / omega : 0.0;
+        p.b_max = s->b_max;
+    }
+    p.seed = s->seed;
+    p.first = first;
+    p.n = n;
+    p.ld = ld;
+    p.y0 = y0;
+    p.phi0 = phi0;
+    int sms = 0;
+    if (sample_device(&sms) != IA_OK) return IA_ERR_NO_DEVICE;
+    const long long grid = std::min<long long>((n + ia_sample::SAMPLE_THREADS - 1) / ia_sample::SAMPLE_THREADS,
+                                               8LL * sms);
+    ia_sample::k_sample<<<(unsigned)grid, ia_sample::SAMPLE_THREADS, 0, reinterpret_cast<cudaStream_t>(stream)>>>(p);
+    return cudaGetLastError() == cudaSuccess ? IA_OK : IA_ERR_CUDA;
 }
 
 int ia_rcp_check(const double* x, double* y, int64_t n, void* stream)

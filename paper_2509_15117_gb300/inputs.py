@@ -387,3 +387,21 @@ def c5_ftle_grid(n_grid: int = 2048, t_max_s: float = 1e-3):
     y0 = head_on(th, ph, sysd.r0, v0)
     seeds = head_on_seeds(th, ph, sysd.r0, v0, kelvin(E_K))[:, :1, :]
     return sysd, y0, np.zeros(len(th)), seeds
+
+
+def energy_scan_systems(species=C2_SPECIES, n_energies: int = 100, E_min_K: float = 3e-8, E_max_K: float = 1e-3,
+                        r0: float = 20000.0, t_max_s: float = 3e-3, q: float = 0.1):
+    """Cells of the collision-energy scan of Fig. 4: head-on Yb+ collisions, r0 = 20,000 a0, D_e = 1 K,
+    a random rf phase per trajectory, n_energies fixed collision energies log-spaced over
+    [E_min_K, E_max_K] (k_B units) for each species. One system per (species, energy) cell, with the
+    velocity tolerance scaled by that cell's head-on speed. Returns (systems, energies in hartree,
+    species per cell). The paper's energy axis and the longest lifetime are not given; 30 nK .. 1 mK
+    brackets every species' threshold (a few W0^3D), and t_max = 3 ms lets the slowest atoms (Cs at
+    30 nK needs about 0.55 ms to reach the ion from 20,000 a0) collide, form complexes and leave."""
+    systems, energies, names = [], [], []
+    for sp in species:
+        for E_K in np.geomspace(E_min_K, E_max_K, n_energies):
+            systems.append(make_system(sp, De_K=1.0, q=q, a=0.0, r0=r0, t_max_s=t_max_s, E_K=float(E_K)))
+            energies.append(kelvin(float(E_K)))
+            names.append(sp)
+    return systems, np.array(energies), names

@@ -2,7 +2,9 @@
 
 Complex-formation probabilities with binomial (Wilson score) intervals (Fig. 3 and Fig. 4 of the
 paper), mean ion heating with its standard error, the bounce-count histogram (Fig. 1c) and the
-survival curve of complex lifetimes (Fig. 2: fraction of complexes alive after a time t).
+survival curve of complex lifetimes (Fig. 2: fraction of complexes alive after a time t) with
+maximum-likelihood fits of its tail, and for Fig. 4 the heating energy scale W0^3D and a fit of the
+complex probability's threshold energy.
 """
 from __future__ import annotations
 
@@ -47,3 +49,120 @@ def summarize(rec) -> dict:
         "survival_t_us": edges[:-1] * AU_TIME_S * 1e6, "survival": alive,
         "attempts_per_trajectory": float(rec["attempts"]) / n if n else 0.0,
     }
+
+
+# ------------------------------------------------------------------ Fig. 2: the lifetime tail
+
+def lifetime_tail_fit(tau, t_min: float, t_cens: float | None = None) -> dict:
+    """Maximum-likelihood fits of the tail of complex lifetimes tau >= t_min (Fig. 2 discussion:
+    beyond about 20 us the fraction of complexes alive decays as a power law, which marks
+    non-hyperbolic chaos; hyperbolic chaos would decay exponentially).
+
+    - Power law: the survival is S(t) = (t / t_min)^-gamma. Its estimator is
+      gamma = d / sum ln(min(tau, t_cens) / t_min), the Hill estimator with right censoring.
+    - Exponential: S(t) = exp(-lambda (t - t_min)), with lambda = d / sum (min(tau, t_cens) - t_min).
+
+    d is the number of uncensored lifetimes. The lifetimes at or beyond t_cens are censored: complexes
+    still alive when the run stops at t_max. Returns both fits, their log-likelihoods and the standard
+    error gamma / sqrt(d).
+    """
+    tau = np.asarray(tau, dtype=np.float64)
+    tau = tau[tau >= t_min]
+    if t_cens is None:
+        t_cens = math.inf
+    cens = tau >= t_cens
+    x = np.minimum(tau, t_cens)
+    d = int((~cens).sum())
+    n = int(tau.size)
+    if d == 0:
+        return {"n": n, "uncensored": 0, "gamma": math.nan, "gamma_se": math.nan, "rate": math.nan,
+                "loglik_power": math.nan, "loglik_exp": math.nan}
+    slog = float(np.log(x / t_min).sum())
+    sexc = float((x - t_min).sum())
+    gamma = d / slog
+    rate = d / sexc
+    # log-likelihoods of the uncensored densities and the censored survivals
+    ll_pow = d * math.log(gamma / t_min) - (gamma + 1.0) * float(np.log(x[~cens] / t_min).sum()) \
+        - gamma * float(np.log(x[cens] / t_min).sum())
+    ll_exp = d * math.log(rate) - rate * sexc
+    return {"n": n, "uncensored": d, "gamma": gamma, "gamma_se": gamma / math.sqrt(d), "rate": rate,
+            "loglik_power": ll_pow, "loglik_exp": ll_exp}
+
+
+def lifetime_tail_fit_binned(hist, k_min: int, ratio: float = math.sqrt(2.0)) -> dict:
+    """Power-law exponent from a histogram of lifetimes over geometric bins (edges t_k = t_0 ratio^k,
+    the ia_stats lifetime bins). Under S(t) ~ t^-gamma the bin index counted from k_min, j = K - k_min,
+    is geometric: P(j) = (1 - p) p^j, where p = ratio^-gamma is the chance of reaching the next bin.
+    The maximum-likelihood p is sum j / (d + sum j), d the uncensored count; the last bin, which also
+    holds everything beyond it, is censored. Returns gamma = -ln p / ln ratio and its error from the
+    Fisher information d / (p (1 - p)^2) by the delta method."""
+    h = np.asarray(hist, dtype=np.float64)[k_min:]
+    if h.sum() == 0:
+        return {"n": 0, "gamma": math.nan, "gamma_se": math.nan}
+    j = np.arange(h.size, dtype=np.float64)
+    d = float(h[:-1].sum())
+    s = float((j * h).sum())
+    p = s / (d + s)
+    gamma = -math.log(p) / math.log(ratio)
+    se = math.sqrt(p * (1.0 - p) ** 2 / max(d, 1.0)) / p / math.log(ratio) if 0 < p < 1 else math.nan
+    return {"n": int(h.sum()), "uncensored": int(d), "gamma": gamma, "gamma_se": se}
+
+
+# ------------------------------------------------------------------ Fig. 4: the energy threshold
+
+def w0_3d(m_atom: float, m_ion: float, Omega: float, a_x: float, q_x: float, C4: float) -> float:
+    """Heating energy scale of a sympathetically cooled rf-trapped ion (Cetina, Grier & Vuletic 2012),
+    as the paper writes it in the discussion of Fig. 4:
+    W0 = 8 / (3 pi) (m_a / (m_i + m_a))^(5/3) (m_i^2 omega^4 C4 / q_x^2)^(1/3),
+    omega = (Omega / 2) sqrt(a_x + q_x^2 / 2). Atomic units in, hartree out."""
+    omega = 0.5 * Omega * math.sqrt(a_x + 0.5 * q_x * q_x)
+    mass = (m_atom / (m_ion + m_atom)) ** (5.0 / 3.0)
+    return 8.0 / (3.0 * math.pi) * mass * (m_ion ** 2 * omega ** 4 * C4 / (q_x * q_x)) ** (1.0 / 3.0)
+
+
+def _tanh_model(lnE, p0, ln_th, width):
+    return 0.5 * p0 * (1.0 - np.tanh((lnE - ln_th) / width))
+
+
+def fit_threshold(E, k, n) -> dict:
+    """Fit P(E) = P0 (1 - tanh((ln E - ln E_th) / w)) / 2 to complex counts k out of n at energies E
+    (Fig. 4: the complex probability falls like a negative tanh up to a threshold energy). Binomial
+    maximum likelihood: a grid over (ln E_th, w) with P0 profiled out, then local refinement of the grid
+    cell. Returns E_th (units of E), w, P0 and the log-likelihood."""
+    lnE = np.log(np.asarray(E, dtype=np.float64))
+    k = np.asarray(k, dtype=np.float64)
+    n = np.asarray(n, dtype=np.float64)
+
+    def loglik(ln_th, width, p0):
+        p = np.clip(_tanh_model(lnE, p0, ln_th, width), 1e-12, 1 - 1e-12)
+        return float((k * np.log(p) + (n - k) * np.log1p(-p)).sum())
+
+    def best_p0(ln_th, width):
+        shape = 0.5 * (1.0 - np.tanh((lnE - ln_th) / width))
+        grid = np.linspace(0.01, 1.0, 100)
+        lls = [loglik(ln_th, width, g) for g in grid]
+        g = grid[int(np.argmax(lls))]
+        fine = np.linspace(max(0.001, g - 0.01), min(1.0, g + 0.01), 41)
+        lls = [loglik(ln_th, width, f) for f in fine]
+        i = int(np.argmax(lls))
+        return fine[i], lls[i], shape
+
+    lo, hi = float(lnE.min()), float(lnE.max())
+    best = (-math.inf, None)
+    for ln_th in np.linspace(lo, hi, 61):
+        for width in np.geomspace(0.05, 0.5 * (hi - lo) + 0.1, 30):
+            p0, ll, _ = best_p0(ln_th, width)
+            if ll > best[0]:
+                best = (ll, (ln_th, width, p0))
+    ln_th, width, p0 = best[1]
+    step_t, step_w = (hi - lo) / 60.0, width * 0.12
+    for _ in range(3):
+        cands = [(t, w) for t in np.linspace(ln_th - step_t, ln_th + step_t, 11)
+                 for w in np.linspace(max(0.02, width - step_w), width + step_w, 11)]
+        for t, w in cands:
+            pp, ll, _ = best_p0(t, w)
+            if ll > best[0]:
+                best = (ll, (t, w, pp))
+        ln_th, width, p0 = best[1]
+        step_t, step_w = step_t / 5.0, step_w / 5.0
+    return {"E_th": math.exp(ln_th), "width_ln": width, "P0": p0, "loglik": best[0]}

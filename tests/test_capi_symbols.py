@@ -108,3 +108,40 @@ def test_adjoint_structs_and_scratch_arithmetic_without_gpu():
     # default warps need the device's occupancy, hence a system
     with pytest.raises(Bd.IaError):
         Bd.ia_adjoint_scratch_bytes(None, 10)
+
+
+def test_sampler_struct_and_argument_checks_without_gpu():
+    assert ctypes.sizeof(Bd.ia_sampler) == 4 * 4 + 8 * 12 + 8
+    L = Bd.load()
+    from paper_2509_15117_gb300 import inputs as I
+    d = I.make_system("Rb").as_dict()
+    good = Bd.make_sampler(Bd.IA_SAMPLE_DISK, d, seed=1, kT=1e-9, kT_ion=1e-11, b_max=2000.0)
+    buf = (ctypes.c_double * 16)()
+    y, ph = ctypes.addressof(buf), ctypes.addressof(buf) + 8 * 12
+    # n = 0 is a no-op; every rejection below happens before any CUDA call
+    assert L.ia_sample_ics(ctypes.byref(good), 0, 0, None, None, 0, None) == 0
+    assert L.ia_sample_ics(None, 0, 1, y, ph, 1, None) == -1
+    assert L.ia_sample_ics(ctypes.byref(good), 0, -1, y, ph, 1, None) == -1
+    assert L.ia_sample_ics(ctypes.byref(good), -5, 1, y, ph, 1, None) == -1
+    assert L.ia_sample_ics(ctypes.byref(good), 2 ** 63 - 1, 2, y, ph, 2, None) == -1
+    assert L.ia_sample_ics(ctypes.byref(good), 0, 2, y, ph, 1, None) == -1          # ld < n
+    assert L.ia_sample_ics(ctypes.byref(good), 0, 1, y + 4, ph, 1, None) == -4      # unaligned
+    bad = [
+        Bd.make_sampler(7, d, seed=1, kT=1e-9),
+        Bd.make_sampler(Bd.IA_SAMPLE_HEAD_ON, d, seed=1, E=0.0),
+        Bd.make_sampler(Bd.IA_SAMPLE_SPHERE, d, seed=1, kT=-1.0),
+        Bd.make_sampler(Bd.IA_SAMPLE_SPHERE, d, seed=1, kT=1e-9, kT_ion=-1e-12),
+        Bd.make_sampler(Bd.IA_SAMPLE_DISK, d, seed=1, kT=1e-9, b_max=d["r0"]),
+        Bd.make_sampler(Bd.IA_SAMPLE_HEAD_ON, d, seed=1, E=1e-9, random_phase=False, phase=float("nan")),
+        Bd.make_sampler(Bd.IA_SAMPLE_SPHERE, dict(d, q=(0.0, 0.0, 0.0)), seed=1, kT=1e-9, kT_ion=1e-12),
+    ]
+    for s in bad:
+        assert L.ia_sample_ics(ctypes.byref(s), 0, 1, y, ph, 1, None) == -1
+    s = Bd.make_sampler(Bd.IA_SAMPLE_SPHERE, d, seed=1, kT=1e-9)
+    s.rf_sign = 0
+    assert L.ia_sample_ics(ctypes.byref(s), 0, 1, y, ph, 1, None) == -1
+    # raw generator
+    assert L.ia_philox4x64(1, 2, 3, 0, 0, None, None) == 0
+    assert L.ia_philox4x64(1, 2, 3, 0, 1, None, None) == -1
+    assert L.ia_philox4x64(1, 2, 3, -1, 1, y, None) == -1
+    assert L.ia_philox4x64(1, 2, 3, 0, 1, y + 4, None) == -4
