@@ -372,8 +372,11 @@ def energy_scan(args):
         fit = St.fit_threshold(E, k, m)
         d0 = systems[cells[0]]
         w0 = St.w0_3d(d0.m_atom, d0.m_ion, d0.Omega, d0.a[0], d0.q[0], 0.5 * d0.alpha)
-        per_species[sp] = {"E_threshold_uK": fit["E_th"] / I.K_TO_HARTREE * 1e6, "W0_3D_uK": w0 / I.K_TO_HARTREE * 1e6,
-                           "threshold_over_W0": fit["E_th"] / w0, "P0": fit["P0"], "width_ln_E": fit["width_ln"],
+        uK = 1e6 / I.K_TO_HARTREE
+        per_species[sp] = {"E_threshold_uK": fit["E_th"] * uK, "E_end_uK": fit["E_end"] * uK, "W0_3D_uK": w0 * uK,
+                           "threshold_over_W0": fit["E_th"] / w0, "end_over_W0": fit["E_end"] / w0,
+                           "P0": fit["P0"], "P_inf": fit["P_inf"], "width_ln_E": fit["width_ln"],
+                           "chi2_per_dof": fit["chi2"] / max(fit["dof"], 1),
                            "P_complex_lowest_E": float(k[0] / m[0]), "P_complex_highest_E": float(k[-1] / m[-1])}
     desc = (f"collision-energy scan: Yb+ head-on with {', '.join(dict.fromkeys(names))}, "
             f"{n_cells // len(per_species)} energies 30 nK..1 mK, {n_per} trajectories per energy, r0 = 20,000 a0, "

@@ -120,49 +120,50 @@ def w0_3d(m_atom: float, m_ion: float, Omega: float, a_x: float, q_x: float, C4:
     return 8.0 / (3.0 * math.pi) * mass * (m_ion ** 2 * omega ** 4 * C4 / (q_x * q_x)) ** (1.0 / 3.0)
 
 
-def _tanh_model(lnE, p0, ln_th, width):
-    return 0.5 * p0 * (1.0 - np.tanh((lnE - ln_th) / width))
-
-
 def fit_threshold(E, k, n) -> dict:
-    """Fit P(E) = P0 (1 - tanh((ln E - ln E_th) / w)) / 2 to complex counts k out of n at energies E
-    (Fig. 4: the complex probability falls like a negative tanh up to a threshold energy). Binomial
-    maximum likelihood: a grid over (ln E_th, w) with P0 profiled out, then local refinement of the grid
-    cell. Returns E_th (units of E), w, P0 and the log-likelihood."""
+    """Fit P(E) = P_inf + (P0 - P_inf) (1 - tanh((ln E - ln E_th) / w)) / 2 to complex counts k out
+    of n at energies E. This is the Fig. 4 trend: the complex probability falls like a negative tanh
+    up to a threshold energy. P_inf is what remains above the threshold; the paper's curves fall to
+    zero.
+
+    The fit is weighted least squares with the binomial variances (floored at 1/n). For each
+    (ln E_th, w) on a grid, the two amplitudes enter linearly and are solved exactly. The best grid
+    cell is refined three times. Returns:
+      - E_th, the midpoint of the fall, in the units of E;
+      - E_end = E_th e^w, where the fall has covered 88 % of P0 - P_inf (tanh 1 = 0.76);
+      - w, P0, P_inf and chi2.
+    """
     lnE = np.log(np.asarray(E, dtype=np.float64))
     k = np.asarray(k, dtype=np.float64)
     n = np.asarray(n, dtype=np.float64)
+    f = k / n
+    wt = n / np.maximum(f * (1.0 - f), 1.0 / n)
 
-    def loglik(ln_th, width, p0):
-        p = np.clip(_tanh_model(lnE, p0, ln_th, width), 1e-12, 1 - 1e-12)
-        return float((k * np.log(p) + (n - k) * np.log1p(-p)).sum())
-
-    def best_p0(ln_th, width):
-        shape = 0.5 * (1.0 - np.tanh((lnE - ln_th) / width))
-        grid = np.linspace(0.01, 1.0, 100)
-        lls = [loglik(ln_th, width, g) for g in grid]
-        g = grid[int(np.argmax(lls))]
-        fine = np.linspace(max(0.001, g - 0.01), min(1.0, g + 0.01), 41)
-        lls = [loglik(ln_th, width, f) for f in fine]
-        i = int(np.argmax(lls))
-        return fine[i], lls[i], shape
+    def solve(ln_th, width):
+        sh = 0.5 * (1.0 - np.tanh((lnE - ln_th) / width))
+        A = np.stack([1.0 - sh, sh], axis=1)  # columns: P_inf, P0
+        Aw = A * wt[:, None]
+        coef = np.linalg.lstsq(Aw.T @ A, Aw.T @ f, rcond=None)[0]
+        coef = np.clip(coef, 0.0, 1.0)
+        r = f - A @ coef
+        return float((wt * r * r).sum()), coef
 
     lo, hi = float(lnE.min()), float(lnE.max())
-    best = (-math.inf, None)
-    for ln_th in np.linspace(lo, hi, 61):
-        for width in np.geomspace(0.05, 0.5 * (hi - lo) + 0.1, 30):
-            p0, ll, _ = best_p0(ln_th, width)
-            if ll > best[0]:
-                best = (ll, (ln_th, width, p0))
-    ln_th, width, p0 = best[1]
-    step_t, step_w = (hi - lo) / 60.0, width * 0.12
+    best = (math.inf, None)
+    for ln_th in np.linspace(lo, hi, 81):
+        for width in np.geomspace(0.05, hi - lo, 40):
+            c2, coef = solve(ln_th, width)
+            if c2 < best[0]:
+                best = (c2, (ln_th, width, coef))
+    ln_th, width, coef = best[1]
+    step_t, step_w = (hi - lo) / 80.0, width * 0.2
     for _ in range(3):
-        cands = [(t, w) for t in np.linspace(ln_th - step_t, ln_th + step_t, 11)
-                 for w in np.linspace(max(0.02, width - step_w), width + step_w, 11)]
-        for t, w in cands:
-            pp, ll, _ = best_p0(t, w)
-            if ll > best[0]:
-                best = (ll, (t, w, pp))
-        ln_th, width, p0 = best[1]
+        for t in np.linspace(ln_th - step_t, ln_th + step_t, 11):
+            for w in np.linspace(max(0.02, width - step_w), width + step_w, 11):
+                c2, cf = solve(t, w)
+                if c2 < best[0]:
+                    best = (c2, (t, w, cf))
+        ln_th, width, coef = best[1]
         step_t, step_w = step_t / 5.0, step_w / 5.0
-    return {"E_th": math.exp(ln_th), "width_ln": width, "P0": p0, "loglik": best[0]}
+    return {"E_th": math.exp(ln_th), "E_end": math.exp(ln_th + width), "width_ln": width,
+            "P0": float(coef[1]), "P_inf": float(coef[0]), "chi2": best[0], "dof": int(len(f) - 4)}

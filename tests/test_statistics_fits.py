@@ -82,17 +82,21 @@ def test_w0_scaling_laws():
     assert 1e-6 < w / I.K_TO_HARTREE < 1e-4
 
 
-def test_threshold_fit_recovers_a_negative_tanh():
+@pytest.mark.parametrize("p_inf", [0.0, 0.1])
+def test_threshold_fit_recovers_a_negative_tanh(p_inf):
     rng = np.random.default_rng(5)
     E = np.geomspace(1e-7, 1e-3, 100)
     p0, th, width = 0.6, 3e-5, 0.8
-    p = 0.5 * p0 * (1 - np.tanh((np.log(E) - math.log(th)) / width))
+    p = p_inf + (p0 - p_inf) * 0.5 * (1 - np.tanh((np.log(E) - math.log(th)) / width))
     n = np.full(100, 10_000)
     k = rng.binomial(n, p)
     f = St.fit_threshold(E, k, n)
     assert f["E_th"] == pytest.approx(th, rel=0.05)
     assert f["width_ln"] == pytest.approx(width, rel=0.05)
     assert f["P0"] == pytest.approx(p0, abs=0.01)
+    assert f["P_inf"] == pytest.approx(p_inf, abs=0.005)
+    assert f["chi2"] < 2.0 * f["dof"]
+    assert f["E_end"] == pytest.approx(th * math.exp(width), rel=0.08)
 
 
 def test_energy_scan_cells():
