@@ -72,12 +72,13 @@ def parse():
                    help="trajectories of the differentiation workload timed through the tangent and adjoint "
                         "kernels (0: skip)")
     p.add_argument("--workload", default="sweep",
-                   choices=["sweep", "thermal", "mixed-graph", "ftle", "sampler", "energy-scan"],
+                   choices=["sweep", "thermal", "mixed-graph", "ftle", "sampler", "energy-scan", "thermal-sweep"],
                    help="sweep: the species x energy step (the bench line); thermal: the Monte Carlo bath; "
                         "mixed-graph: the 250-cell parameter sweep replayed as one CUDA graph with statistics; "
                         "ftle: the tangent kernel on the FTLE grid; sampler: initial conditions drawn on the "
                         "device; energy-scan: the collision-energy scan with device-drawn initial conditions, "
-                        "per-cell statistics and the threshold fit")
+                        "per-cell statistics and the threshold fit; thermal-sweep: the species x T x D_e "
+                        "thermal runs with the paper's sphere sampler on the device")
     p.add_argument("--scale", type=float, default=0.0, help="size factor of the secondary workloads")
     p.add_argument("--sampler-sample", type=int, default=1 << 24,
                    help="trajectories whose initial conditions are drawn on the device, per sampler kind, "
@@ -171,6 +172,9 @@ def secondary(args):
     from paper_2509_15117_gb300 import schedule as Sch
     if args.workload == "energy-scan":
         energy_scan(args)
+        return
+    if args.workload == "thermal-sweep":
+        thermal_sweep(args)
         return
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -385,6 +389,90 @@ def energy_scan(args):
                       "trajectories": n, "attempted_steps_per_trajectory": att / n, "max_attempted_steps": mx,
                       "wait_errors": waits, "gpu_launches": n_cells + 4, "dtype": "f64", "data": "synthetic",
                       "config": {"workload": desc, "rtol": 1e-10}, "per_species": per_species}), flush=True)
+
+
+def thermal_sweep(args):
+    """Fig. 3 workload: the paper's thermal runs (atom uniform on the r0 sphere, Gaussian velocity flipped
+    inward, ion Gaussian at 10 uK, random rf phase) drawn on the device for every (species, T, D_e)
+    cell, one persistent launch over all cells, per-cell statistics; then the complex probability per
+    cell with its 3-sigma Wilson interval and the trends the text states (fewer complexes when hotter,
+    more when heavier, no change between D_e = 1 K and 100 K). The paper runs 10^7 per cell; --scale
+    is that fraction (default 1e-3)."""
+    import torch
+    from paper_2509_15117_gb300 import binding as Bd
+    from paper_2509_15117_gb300 import schedule as Sch
+    from paper_2509_15117_gb300 import statistics as St
+    scale = args.scale if args.scale > 0 else 1e-3
+    n_per = max(1, int(round(scale * 1e7)))
+    systems, cells = I.thermal_sweep_systems()
+    descs = [s_.as_dict() for s_ in systems]
+    n_cells = len(descs)
+    n = n_per * n_cells
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    y = torch.empty((12, n), dtype=torch.float64, device="cuda")
+    ph = torch.empty((n,), dtype=torch.float64, device="cuda")
+    sid = torch.arange(n_cells, dtype=torch.int32, device="cuda").repeat_interleave(n_per)
+    speeds = [s_.atol_vel / 1e-10 for s_ in systems]
+    order = torch.from_numpy(Sch.order_by_cost(sid.cpu().numpy(), Sch.system_cost(systems, speeds))).cuda()
+    samplers = [Bd.make_sampler(Bd.IA_SAMPLE_SPHERE, descs[c], 3100, kT=I.kelvin(cells[c][1]),
+                                kT_ion=I.kelvin(10e-6)) for c in range(n_cells)]
+    with Bd.System(descs) as S:
+        out = Bd.alloc_obs(n)
+        st = Bd.alloc_stats(n_cells)
+        Bd.ia_reserve(S.handle, n, kernel=Bd.IA_KERNEL_PERSISTENT)
+        Bd.ia_reserve_stats(S.handle, n, n_cells)
+        hot = max(range(n_cells), key=lambda c: cells[c][1])  # warm-up on a 1 mK cell: short trajectories
+        for _ in range(args.warmup):
+            m = min(256, n_per)
+            Bd.ia_sample_ics(samplers[hot], hot * n_per, y[:, :m], ph[:m])
+            Bd.ia_launch(S.handle, y[:, :m], ph[:m], torch.full((m,), hot, dtype=torch.int32, device="cuda"),
+                         Bd.alloc_obs(m))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        for c in range(n_cells):
+            a = c * n_per
+            Bd.ia_sample_ics(samplers[c], a, y[:, a:a + n_per], ph[a:a + n_per])
+        Bd.ia_launch(S.handle, y, ph, sid, out, order=order)
+        Bd.ia_reduce_stats(S.handle, out, n, sid, n_cells, st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        waits = Bd.ia_launch_phases(S.handle)[2]
+        stats = Bd.stats_to_numpy(st)
+        att = int((out["n_steps"].to(torch.int64) + out["n_rej"].to(torch.int64)).sum().item())
+        mx = int((out["n_steps"] + out["n_rej"]).max().item())
+    table = {}
+    for c, (sp, T, De) in enumerate(cells):
+        sm = St.summarize(stats[c])
+        table[f"{sp} T={T * 1e6:g}uK De={De:g}K"] = {
+            "P_complex": sm["P_complex"], "P_complex_3sigma": list(sm["P_complex_3sigma"]),
+            "mean_dE_ion_uK": sm["mean_dE_ion"] / I.K_TO_HARTREE * 1e6}
+    P = {cells[c]: St.summarize(stats[c])["P_complex"] for c in range(n_cells)}
+    lo_hi = {cells[c]: St.summarize(stats[c])["P_complex_3sigma"] for c in range(n_cells)}
+    sp_list = list(dict.fromkeys(cl[0] for cl in cells))
+    temps = sorted(set(cl[1] for cl in cells))
+    depths = sorted(set(cl[2] for cl in cells))
+    trends = {
+        "falls_with_T": all(P[(sp, temps[i], De)] >= P[(sp, temps[i + 1], De)]
+                            for sp in sp_list for De in depths for i in range(len(temps) - 1)),
+        "rises_with_mass": all(P[(sp_list[i], T, De)] <= P[(sp_list[i + 1], T, De)]
+                               for T in temps for De in depths for i in range(len(sp_list) - 1)),
+        "De_1K_vs_100K_overlap_3sigma": all(
+            lo_hi[(sp, T, depths[0])][0] <= lo_hi[(sp, T, depths[1])][1] and
+            lo_hi[(sp, T, depths[1])][0] <= lo_hi[(sp, T, depths[0])][1] for sp in sp_list for T in temps),
+    }
+    desc = (f"thermal runs (Fig. 3): Yb+ with {', '.join(sp_list)} x T = {', '.join(f'{t * 1e6:g} uK' for t in temps)} "
+            f"x D_e = {', '.join(f'{d:g} K' for d in depths)}, {n_per} trajectories per cell; atom uniform on the "
+            f"5000 a0 sphere, Gaussian velocity flipped inward, ion Gaussian at 10 uK, random rf phase; "
+            f"drawn on the device (sphere sampler, seed 3100)")
+    print(json.dumps({"metric": METRIC, "workload": "thermal-sweep", "value": n / (ms / 1e3), "unit": UNIT,
+                      "ms": ms, "trajectories": n, "attempted_steps_per_trajectory": att / n,
+                      "max_attempted_steps": mx, "wait_errors": waits, "gpu_launches": n_cells + 4,
+                      "dtype": "f64", "data": "synthetic", "config": {"workload": desc, "rtol": 1e-10},
+                      "trends": trends, "cells": table}), flush=True)
 
 
 def dist_env():

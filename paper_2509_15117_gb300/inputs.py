@@ -405,3 +405,24 @@ def energy_scan_systems(species=C2_SPECIES, n_energies: int = 100, E_min_K: floa
             energies.append(kelvin(float(E_K)))
             names.append(sp)
     return systems, np.array(energies), names
+
+
+FIG3_TEMPS_K = (10e-6, 100e-6, 1e-3)
+FIG3_DEPTHS_K = (1.0, 100.0)
+
+
+def thermal_sweep_systems(species=C2_SPECIES, temps_K=FIG3_TEMPS_K, depths_K=FIG3_DEPTHS_K, t_max_s: float = 1e-3):
+    """Cells of the thermal runs of Fig. 3: Yb+ with each species, bath temperature T and well depth
+    D_e (1 K and 100 K, the caption's two depths), r0 = 5000 a0, q = 0.1. The caption gives no
+    temperatures; 10 uK, 100 uK and 1 mK span the range the text discusses. One system per cell, with
+    the velocity tolerance scaled by that cell's thermal speed sqrt(k_B T / m_a). Returns (systems,
+    cells as (species, T_K, De_K))."""
+    systems, cells = [], []
+    for sp in species:
+        m_a = SPECIES[sp]["mass_amu"] * AMU_TO_ME
+        for T in temps_K:
+            for De in depths_K:
+                vth = math.sqrt(kelvin(T) / m_a)
+                systems.append(make_system(sp, De_K=De, q=0.1, a=0.0, r0=5000.0, t_max_s=t_max_s, v_scale=vth))
+                cells.append((sp, T, De))
+    return systems, cells

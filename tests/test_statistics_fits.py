@@ -111,3 +111,15 @@ def test_energy_scan_cells():
         assert 10 * abs(V) < e
         assert s.atol_vel == pytest.approx(1e-10 * math.sqrt(2 * e / s.m_atom), rel=1e-12)
     assert E.min() == pytest.approx(I.kelvin(3e-8)) and E.max() == pytest.approx(I.kelvin(1e-3))
+
+
+def test_thermal_sweep_cells():
+    """Fig. 3 cells: 5 species x 3 temperatures x 2 well depths, r0 = 5000 a0 meeting 10 |V(r0)| < kT,
+    velocity tolerance scaled by the cell's thermal speed."""
+    systems, cells = I.thermal_sweep_systems()
+    assert len(systems) == 30 and len(set(cells)) == 30
+    for s, (sp, T, De) in zip(systems, cells):
+        assert s.De == pytest.approx(I.kelvin(De))
+        C4 = 0.5 * s.alpha
+        assert 10 * C4 / s.r0 ** 4 < I.kelvin(T)
+        assert s.atol_vel == pytest.approx(1e-10 * math.sqrt(I.kelvin(T) / s.m_atom), rel=1e-12)
