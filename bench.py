@@ -72,13 +72,15 @@ def parse():
                    help="trajectories of the differentiation workload timed through the tangent and adjoint "
                         "kernels (0: skip)")
     p.add_argument("--workload", default="sweep",
-                   choices=["sweep", "thermal", "mixed-graph", "ftle", "sampler", "energy-scan", "thermal-sweep"],
+                   choices=["sweep", "thermal", "mixed-graph", "ftle", "sampler", "energy-scan", "thermal-sweep",
+                            "lifetimes"],
                    help="sweep: the species x energy step (the bench line); thermal: the Monte Carlo bath; "
                         "mixed-graph: the 250-cell parameter sweep replayed as one CUDA graph with statistics; "
                         "ftle: the tangent kernel on the FTLE grid; sampler: initial conditions drawn on the "
                         "device; energy-scan: the collision-energy scan with device-drawn initial conditions, "
                         "per-cell statistics and the threshold fit; thermal-sweep: the species x T x D_e "
-                        "thermal runs with the paper's sphere sampler on the device")
+                        "thermal runs with the paper's sphere sampler on the device; lifetimes: complex "
+                        "lifetimes per species and the fit of their tail")
     p.add_argument("--scale", type=float, default=0.0, help="size factor of the secondary workloads")
     p.add_argument("--sampler-sample", type=int, default=1 << 24,
                    help="trajectories whose initial conditions are drawn on the device, per sampler kind, "
@@ -175,6 +177,9 @@ def secondary(args):
         return
     if args.workload == "thermal-sweep":
         thermal_sweep(args)
+        return
+    if args.workload == "lifetimes":
+        lifetimes(args)
         return
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -473,6 +478,86 @@ def thermal_sweep(args):
                       "max_attempted_steps": mx, "wait_errors": waits, "gpu_launches": n_cells + 4,
                       "dtype": "f64", "data": "synthetic", "config": {"workload": desc, "rtol": 1e-10},
                       "trends": trends, "cells": table}), flush=True)
+
+
+def lifetimes(args):
+    """Fig. 2 workload: head-on collisions of each species with Yb+ at E = 1.5 uK, D_e = 1 K, r0 = 5000 a0,
+    rf phase 0, (theta, phi) uniform on the octant and drawn on the device; one persistent launch over
+    all species, per-species statistics; then the survival of complex lifetimes (t_last_bounce -
+    t_first_bounce) and the maximum-likelihood fit of its tail beyond 20 us. A complex still alive at
+    t_max is censored at its observed lifetime. --scale sets the trajectories per species in units of
+    10^5 (default 0.2)."""
+    import torch
+    from paper_2509_15117_gb300 import binding as Bd
+    from paper_2509_15117_gb300 import schedule as Sch
+    from paper_2509_15117_gb300 import statistics as St
+    scale = args.scale if args.scale > 0 else 0.2
+    n_per = max(1, int(round(scale * 1e5)))
+    E_K = 1.5e-6
+    species = I.C2_SPECIES
+    systems = [I.make_system(sp, De_K=1.0, q=0.1, a=0.0, r0=5000.0, t_max_s=1e-3, E_K=E_K) for sp in species]
+    descs = [s_.as_dict() for s_ in systems]
+    n_cells = len(descs)
+    n = n_per * n_cells
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    y = torch.empty((12, n), dtype=torch.float64, device="cuda")
+    ph = torch.empty((n,), dtype=torch.float64, device="cuda")
+    sid = torch.arange(n_cells, dtype=torch.int32, device="cuda").repeat_interleave(n_per)
+    speeds = [s_.atol_vel / 1e-10 for s_ in systems]
+    order = torch.from_numpy(Sch.order_by_cost(sid.cpu().numpy(), Sch.system_cost(systems, speeds))).cuda()
+    samplers = [Bd.make_sampler(Bd.IA_SAMPLE_HEAD_ON, descs[c], 2002, E=I.kelvin(E_K), random_phase=False,
+                                phase=0.0) for c in range(n_cells)]
+    with Bd.System(descs) as S:
+        out = Bd.alloc_obs(n)
+        st = Bd.alloc_stats(n_cells)
+        Bd.ia_reserve(S.handle, n, kernel=Bd.IA_KERNEL_PERSISTENT)
+        Bd.ia_reserve_stats(S.handle, n, n_cells)
+        for _ in range(args.warmup):  # 256 Li trajectories
+            Bd.ia_sample_ics(samplers[0], 0, y[:, :256], ph[:256])
+            Bd.ia_launch(S.handle, y[:, :256], ph[:256], sid[:256].contiguous(), Bd.alloc_obs(256))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        for c in range(n_cells):
+            a = c * n_per
+            Bd.ia_sample_ics(samplers[c], a, y[:, a:a + n_per], ph[a:a + n_per])
+        Bd.ia_launch(S.handle, y, ph, sid, out, order=order)
+        Bd.ia_reduce_stats(S.handle, out, n, sid, n_cells, st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        waits = Bd.ia_launch_phases(S.handle)[2]
+        stats = Bd.stats_to_numpy(st)
+        g = Bd.to_numpy(out)
+    us = I.AU_TIME_S * 1e6
+    t_min_us = 20.0
+    k_min = int(math.floor(2.0 * (math.log2(t_min_us / us) - 20.0)))  # first lifetime bin at or after 20 us
+    per_species = {}
+    for c, sp in enumerate(species):
+        sl = slice(c * n_per, (c + 1) * n_per)
+        cx = g["n_bounce"][sl] >= 2
+        tau = (g["t_last_bounce"][sl] - g["t_first_bounce"][sl])[cx] * us
+        cens = ((g["status"][sl] & Bd.ST_TMAX) != 0)[cx]
+        fit = St.lifetime_tail_fit(tau, t_min_us, censored=cens)
+        binned = St.lifetime_tail_fit_binned(stats["lifetime_hist"][c], k_min + 1)
+        alive = {f"{t:g}us": float((tau >= t).mean()) if tau.size else 0.0 for t in (1, 20, 100, 300, 600)}
+        per_species[sp] = {"complexes": int(cx.sum()), "P_complex": float(cx.mean()), "alive_after": alive,
+                           "beyond_20us": fit["n"], "censored_at_t_max": int(cens.sum()),
+                           "gamma": fit["gamma"], "gamma_se": fit["gamma_se"],
+                           "loglik_power_minus_exp": fit["loglik_power"] - fit["loglik_exp"],
+                           "gamma_from_bins": binned["gamma"], "gamma_from_bins_se": binned["gamma_se"]}
+    desc = (f"complex lifetimes (Fig. 2): Yb+ head-on with {', '.join(species)} at E = 1.5 uK, D_e = 1 K, "
+            f"r0 = 5000 a0, q = 0.1, rf phase 0, t_max = 1 ms, {n_per} trajectories per species with (theta, phi) "
+            f"uniform on the octant drawn on the device (seed 2002)")
+    att = int((g["n_steps"].astype(np.int64) + g["n_rej"]).sum())
+    print(json.dumps({"metric": METRIC, "workload": "lifetimes", "value": n / (ms / 1e3), "unit": UNIT, "ms": ms,
+                      "trajectories": n, "attempted_steps_per_trajectory": att / n,
+                      "max_attempted_steps": int((g["n_steps"].astype(np.int64) + g["n_rej"]).max()),
+                      "wait_errors": waits, "gpu_launches": n_cells + 4, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": desc, "rtol": 1e-10, "tail_fit_from_us": t_min_us},
+                      "per_species": per_species}), flush=True)
 
 
 def dist_env():

@@ -53,7 +53,7 @@ def summarize(rec) -> dict:
 
 # ------------------------------------------------------------------ Fig. 2: the lifetime tail
 
-def lifetime_tail_fit(tau, t_min: float, t_cens: float | None = None) -> dict:
+def lifetime_tail_fit(tau, t_min: float, t_cens: float | None = None, censored=None) -> dict:
     """Maximum-likelihood fits of the tail of complex lifetimes tau >= t_min (Fig. 2 discussion:
     beyond about 20 us the fraction of complexes alive decays as a power law, which marks
     non-hyperbolic chaos; hyperbolic chaos would decay exponentially).
@@ -62,15 +62,18 @@ def lifetime_tail_fit(tau, t_min: float, t_cens: float | None = None) -> dict:
       gamma = d / sum ln(min(tau, t_cens) / t_min), the Hill estimator with right censoring.
     - Exponential: S(t) = exp(-lambda (t - t_min)), with lambda = d / sum (min(tau, t_cens) - t_min).
 
-    d is the number of uncensored lifetimes. The lifetimes at or beyond t_cens are censored: complexes
-    still alive when the run stops at t_max. Returns both fits, their log-likelihoods and the standard
-    error gamma / sqrt(d).
+    d is the number of uncensored lifetimes. Censored lifetimes are lower bounds: complexes still alive
+    when the run stopped. They are those at or beyond a common t_cens, or those flagged in `censored`
+    (one flag per lifetime, for runs whose complexes started at different times before t_max).
+    Returns both fits, their log-likelihoods and the standard error gamma / sqrt(d).
     """
     tau = np.asarray(tau, dtype=np.float64)
-    tau = tau[tau >= t_min]
+    flag = np.zeros(tau.shape, dtype=bool) if censored is None else np.asarray(censored, dtype=bool)
+    keep = tau >= t_min
+    tau, flag = tau[keep], flag[keep]
     if t_cens is None:
         t_cens = math.inf
-    cens = tau >= t_cens
+    cens = (tau >= t_cens) | flag
     x = np.minimum(tau, t_cens)
     d = int((~cens).sum())
     n = int(tau.size)

@@ -39,6 +39,19 @@ def test_censored_power_law_tail():
     assert f_naive["gamma"] > gamma + 4 * f_naive["gamma_se"]
 
 
+def test_power_law_tail_with_per_lifetime_censoring():
+    """Complexes that start at different times and are all stopped at the same t_max: each lifetime
+    is censored at its own bound, t_max - t_start."""
+    rng = np.random.default_rng(9)
+    gamma, t_min = 0.8, 20.0
+    tau = pareto(80_000, gamma, t_min, seed=11)
+    bound = rng.uniform(200.0, 1000.0, tau.size)
+    cens = tau >= bound
+    f = St.lifetime_tail_fit(np.minimum(tau, bound), t_min, censored=cens)
+    assert f["uncensored"] == int((~cens).sum()) and cens.sum() > 1000
+    assert abs(f["gamma"] - gamma) < 4 * f["gamma_se"]
+
+
 def test_exponential_tail_is_told_apart():
     tau = 20.0 + np.random.default_rng(4).exponential(50.0, 50_000)
     f = St.lifetime_tail_fit(tau, 20.0)
