@@ -420,7 +420,7 @@ typedef struct ia_sampler {
  * Raw generator (no counterpart in the paper): Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11).
  * Block j, j = 0 .. n_blocks - 1, is the ten-round map of the counter (first + j, ctr1, 0, 0) under the
  * key (key0, key1); its four words go to out[4j .. 4j + 3] (device array, 8-byte aligned).
- * first >= 0 and first + n_blocks must not overflow. Asynchronous on `stream`.
+ * first >= 0 and first + n_blocks must not overflow (else IA_ERR_INVALID_ARG). Asynchronous on `stream`.
  */
 int ia_philox4x64(uint64_t key0, uint64_t key1, uint64_t ctr1, int64_t first, int64_t n_blocks, uint64_t* out,
                   void* stream);
@@ -439,7 +439,8 @@ int ia_philox4x64(uint64_t key0, uint64_t key1, uint64_t ctr1, int64_t first, in
  * A trajectory's values depend only on its index, the seed and the kind: any index range can be drawn
  * alone (in chunks, or one range per rank) and matches the whole batch. n = 0 is a no-op.
  * IA_ERR_INVALID_ARG for a parameter out of the ranges above, or when ld < n; IA_ERR_ALIGNMENT for
- * unaligned pointers. Asynchronous on `stream`.
+ * unaligned pointers; IA_ERR_NO_DEVICE when the current device is not an sm_103 GPU. Nothing is written
+ * when a check fails. Asynchronous on `stream`.
  */
 int ia_sample_ics(const ia_sampler* s, int64_t first, int64_t n, double* y0, double* phi0, int64_t ld,
                   void* stream);

@@ -1,4 +1,4 @@
-"""ctypes front end of the CPU FP64 oracle (``ia_oracle.c``).
+"""ctypes front end of the CPU FP64 oracle (``ia_oracle.c`` and ``ia_sample_oracle.c``).
 
 TEST INFRASTRUCTURE, NOT PRODUCT CODE: only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this module. It shares no
@@ -8,7 +8,9 @@ code with the CUDA library; both receive the same seeded initial conditions from
 The C source restates the method of arXiv 2509.15117: Eq. 1's equations of motion, V(r) = C8/r^8 -
 C4/r^4 with C4 = alpha/2 and C8 = C4^2/(4 D_e), the Dormand-Prince 5(4) integrator of Dormand & Prince
 (1980) / Shampine & Reichelt (1997) with ode45's step control, the outward crossing of r0 as the end
-of a head-on or thermal trajectory, and the Fig. 1 observables.
+of a head-on or thermal trajectory, and the Fig. 1 observables. The second source restates the
+Philox4x64-10 generator (Salmon et al., SC'11) and the samplers of the paper's head-on and thermal
+runs, against which the library's device-drawn initial conditions are checked.
 """
 from __future__ import annotations
 
