@@ -56,6 +56,65 @@ class IaError(RuntimeError):
     pass
 
 
+class IaArgumentError(IaError, ValueError):
+    """A tensor handed to the binding lacks the dtype, shape, layout or device the C ABI expects. The
+    C side receives bare pointers and sizes, so these are checked here before any pointer crosses."""
+
+
+def _on_device(t) -> bool:
+    return bool(t.is_cuda)
+
+
+def _tensor(t, name: str, dtype, shape, contiguous: bool = True):
+    """Check one tensor: dtype, rank, sizes (None = any), a dense layout (or, with contiguous=False, a
+    structure-of-arrays layout: unit stride along the last axis, rows at least a row's length apart),
+    and last the device."""
+    import torch
+    if t is None:
+        raise IaArgumentError(f"{name}: missing")
+    if not isinstance(t, torch.Tensor):
+        raise IaArgumentError(f"{name}: expected a torch tensor, got {type(t).__name__}")
+    if t.dtype != dtype:
+        raise IaArgumentError(f"{name}: dtype {t.dtype}, expected {dtype}")
+    if t.dim() != len(shape) or any(w is not None and t.shape[a] != w for a, w in enumerate(shape)):
+        raise IaArgumentError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if t.numel() > 0:
+        if contiguous and not t.is_contiguous():
+            raise IaArgumentError(f"{name}: must be contiguous")
+        if not contiguous and (t.stride(-1) != 1 and t.shape[-1] > 1
+                               or any(t.stride(a) < t.shape[-1] for a in range(t.dim() - 1))):
+            raise IaArgumentError(f"{name}: rows must have unit stride and not overlap, strides {t.stride()}")
+    if not _on_device(t):
+        raise IaArgumentError(f"{name}: must be on a CUDA device")
+    return t
+
+
+def _ic_tensors(y0_soa, phi0, sys_id, order) -> int:
+    import torch
+    _tensor(phi0, "phi0", torch.float64, (None,))
+    n = int(phi0.shape[0])
+    _tensor(y0_soa, "y0_soa", torch.float64, (12, n), contiguous=False)
+    if sys_id is not None:
+        _tensor(sys_id, "sys_id", torch.int32, (n,))
+    if order is not None:
+        _tensor(order, "order", torch.int64, (n,))
+    return n
+
+
+def _obs_tensors(out: dict, n: int) -> None:
+    import torch
+    for f in OBS_FIELDS:
+        dt = torch.float64 if f in ("theta_s", "dp", "dE_ion", "t_final", "t_first_bounce", "t_last_bounce") \
+            else torch.int32
+        if f not in out:
+            raise IaArgumentError(f"out[{f!r}]: missing")
+        _tensor(out[f], f"out[{f!r}]", dt, (None,))
+        if out[f].shape[0] < n:
+            raise IaArgumentError(f"out[{f!r}]: {out[f].shape[0]} elements for {n} trajectories")
+    if out.get("y_final") is not None:
+        _tensor(out["y_final"], "out['y_final']", torch.float64, (12, n))
+
+
 class ia_system_desc(ctypes.Structure):
     _fields_ = [
         ("m_ion", ctypes.c_double), ("m_atom", ctypes.c_double),
@@ -267,6 +326,7 @@ def alloc_obs(n: int, device="cuda", y_final: bool = False) -> dict:
 
 
 def _obs_struct(out: dict, n: int) -> ia_obs_soa:
+    _obs_tensors(out, n)
     o = ia_obs_soa()
     for f in OBS_FIELDS:
         setattr(o, f, out[f].data_ptr())
@@ -306,6 +366,7 @@ def make_opts(kernel: int = IA_KERNEL_PERSISTENT, block: int = 0, grid: int = 0,
     opts.tail_sms = tail_sms
     opts.tail_pair = tail_pair
     if scratch is not None:
+        _tensor(scratch, "scratch", scratch.dtype, (None,) * scratch.dim())
         opts.scratch = scratch.data_ptr()
         opts.scratch_bytes = scratch.numel() * scratch.element_size()
     return opts
@@ -323,6 +384,9 @@ def ia_reserve(handle: int, n: int, **kw) -> None:
 
 
 def ia_rcp_check(x, y, stream=None) -> None:
+    import torch
+    _tensor(x, "x", torch.float64, (None,))
+    _tensor(y, "y", torch.float64, (x.shape[0],))
     _check(load().ia_rcp_check(x.data_ptr(), y.data_ptr(), int(x.numel()), _stream_ptr(stream)))
 
 
@@ -349,7 +413,10 @@ def make_sampler(kind: int, desc: dict, seed: int, E: float = 0.0, kT: float = 0
 def ia_sample_ics(sampler: ia_sampler, first: int, y0_soa, phi0, stream=None) -> None:
     """Fill device tensors y0_soa (12, n) float64 (row stride = ld) and phi0 (n,) with the initial
     conditions of trajectories first .. first + n - 1."""
+    import torch
+    _tensor(phi0, "phi0", torch.float64, (None,))
     n = int(phi0.shape[0])
+    _tensor(y0_soa, "y0_soa", torch.float64, (12, n), contiguous=False)
     ld = int(y0_soa.stride(0)) if n > 0 else 0
     _check(load().ia_sample_ics(ctypes.byref(sampler), int(first), n, y0_soa.data_ptr(), phi0.data_ptr(), ld,
                                 _stream_ptr(stream)))
@@ -357,13 +424,15 @@ def ia_sample_ics(sampler: ia_sampler, first: int, y0_soa, phi0, stream=None) ->
 
 def ia_philox4x64(key0: int, key1: int, ctr1: int, first: int, out, stream=None) -> None:
     """Raw Philox4x64-10 blocks into a device tensor out (n_blocks, 4) of int64 (the words' bits)."""
+    import torch
+    _tensor(out, "out", torch.int64, (None, 4))
     m = 0xFFFFFFFFFFFFFFFF
     _check(load().ia_philox4x64(int(key0) & m, int(key1) & m, int(ctr1) & m, int(first), int(out.shape[0]),
                                 out.data_ptr(), _stream_ptr(stream)))
 
 
 def _ic_struct(y0_soa, phi0, sys_id, order) -> ia_ic_soa:
-    n = int(phi0.shape[0])
+    n = _ic_tensors(y0_soa, phi0, sys_id, order)
     ic = ia_ic_soa()
     ic.y0 = y0_soa.data_ptr()
     ic.phi0 = phi0.data_ptr()
@@ -404,9 +473,22 @@ def alloc_stats(n_cells: int, device="cuda"):
 
 def ia_reduce_stats(handle: int, out: dict, n: int, cell_id, n_cells: int, stats, stream=None) -> None:
     """Reduce device observables into the device stats buffer (see alloc_stats)."""
+    import torch
     o = _obs_struct(out, n)
+    if cell_id is not None:
+        _tensor(cell_id, "cell_id", torch.int32, (None,))
+        if cell_id.shape[0] < n:
+            raise IaArgumentError(f"cell_id: {cell_id.shape[0]} elements for {n} trajectories")
+    _stats_tensor(stats, n_cells)
     _check(load().ia_reduce_stats(handle, ctypes.byref(o), n, cell_id.data_ptr() if cell_id is not None else None,
                                   n_cells, stats.data_ptr(), _stream_ptr(stream)))
+
+
+def _stats_tensor(stats, n_cells: int) -> None:
+    import torch
+    _tensor(stats, "stats", torch.uint8, (None,))
+    if stats.numel() < max(int(n_cells), 0) * STATS_DTYPE.itemsize:
+        raise IaArgumentError(f"stats: {stats.numel()} bytes for {n_cells} records")
 
 
 def ia_reserve_stats(handle: int, n: int, n_cells: int) -> None:
@@ -422,10 +504,16 @@ class Graph:
 
     def __init__(self, handle: int, y0_soa, phi0, sys_id, out: dict, stream, order=None, cell_id=None,
                  n_cells: int = 0, stats=None, **kw):
+        import torch
         n = int(phi0.shape[0])
+        self.ptr = None
         self._keep = (y0_soa, phi0, sys_id, out, order, cell_id, stats)
         ic = _ic_struct(y0_soa, phi0, sys_id, order)
         o = _obs_struct(out, n)
+        if cell_id is not None:
+            _tensor(cell_id, "cell_id", torch.int32, (n,))
+        if stats is not None:
+            _stats_tensor(stats, n_cells)
         opts = make_opts(kernel=IA_KERNEL_PERSISTENT, **kw)
         g = ctypes.c_void_p()
         _check(load().ia_graph_create(handle, ctypes.byref(ic), n, ctypes.byref(o), ctypes.byref(opts),
@@ -474,13 +562,25 @@ def alloc_tangent(n: int, ndir: int, dy_final: bool = False, ftle: bool = True, 
 
 def ia_launch_tangent(handle: int, y0_soa, phi0, sys_id, out: dict, dy0, dq, tan: dict, stream=None) -> None:
     """Tangent launch: dy0 (ndir, 12, n) device float64 (d y0 / d p_k), dq (ndir, 3) host (d q / d p_k)."""
+    import torch
     n = int(phi0.shape[0])
     ic = _ic_struct(y0_soa, phi0, sys_id, None)
     o = _obs_struct(out, n)
-    ti = ia_tangent_in()
+    _tensor(dy0, "dy0", torch.float64, (None, 12, n))
     ndir = int(dy0.shape[0])
-    ti.dy0 = dy0.data_ptr()
+    if not 1 <= ndir <= 4:
+        raise IaArgumentError(f"dy0: {ndir} directions, expected 1..4")
+    for k in ("d_theta_s", "d_dp", "d_dE_ion", "d_t_final"):
+        _tensor(tan.get(k), f"tan[{k!r}]", torch.float64, (ndir, n))
+    if "dy_final" in tan:
+        _tensor(tan["dy_final"], "tan['dy_final']", torch.float64, (ndir, 12, n))
+    if "ftle" in tan:
+        _tensor(tan["ftle"], "tan['ftle']", torch.float64, (n,))
     dq = np.asarray(dq, dtype=np.float64)
+    if dq.ndim != 2 or dq.shape[0] < ndir or dq.shape[1] != 3:
+        raise IaArgumentError(f"dq: shape {dq.shape}, expected ({ndir}, 3)")
+    ti = ia_tangent_in()
+    ti.dy0 = dy0.data_ptr()
     for k in range(ndir):
         for j in range(3):
             ti.dq[k][j] = float(dq[k, j])
@@ -517,6 +617,7 @@ def make_adjoint_opts(seg: int = 0, max_ckpt: int = 0, warps: int = 0, scratch=N
     o.max_ckpt = int(max_ckpt)
     o.warps = int(warps)
     if scratch is not None:
+        _tensor(scratch, "scratch", scratch.dtype, (None,) * scratch.dim())
         o.scratch = scratch.data_ptr()
         o.scratch_bytes = scratch.numel() * scratch.element_size()
     return o
@@ -550,15 +651,27 @@ def ia_launch_adjoint(handle: int, y0_soa, phi0, sys_id, out: dict, adj: dict, d
     (4, 12, n) and adj["grad_q"] (4, 3, n); with seeds dy0 (ndir, 12, n) device and dq (ndir, 3) host,
     their projections into adj["d_theta_s"] .. adj["d_t_final"] (ndir, n). opts: seg, max_ckpt, warps,
     scratch (a device tensor)."""
+    import torch
     n = int(phi0.shape[0])
     ic = _ic_struct(y0_soa, phi0, sys_id, None)
     o = _obs_struct(out, n)
+    if "grad_y0" in adj:
+        _tensor(adj["grad_y0"], "adj['grad_y0']", torch.float64, (4, 12, n))
+    if "grad_q" in adj:
+        _tensor(adj["grad_q"], "adj['grad_q']", torch.float64, (4, 3, n))
     ti = None
     if dy0 is not None:
+        _tensor(dy0, "dy0", torch.float64, (None, 12, n))
         ti = ia_tangent_in()
         ndir = int(dy0.shape[0])
+        if not 1 <= ndir <= 4:
+            raise IaArgumentError(f"dy0: {ndir} directions, expected 1..4")
+        for k in ("d_theta_s", "d_dp", "d_dE_ion", "d_t_final"):
+            _tensor(adj.get(k), f"adj[{k!r}]", torch.float64, (ndir, n))
         ti.dy0 = dy0.data_ptr()
         dqa = np.zeros((4, 3)) if dq is None else np.asarray(dq, dtype=np.float64)
+        if dqa.ndim != 2 or dqa.shape[0] < ndir or dqa.shape[1] != 3:
+            raise IaArgumentError(f"dq: shape {dqa.shape}, expected ({ndir}, 3)")
         for k in range(ndir):
             for j in range(3):
                 ti.dq[k][j] = float(dqa[k, j])
