@@ -685,8 +685,25 @@ def _oracle_sample(seconds: float, steps: int = 1, warmup: int = 0):
                       f"(species x energy sweep, grid stride 4), {t_used:.1f} s on {cores} threads"}
 
 
-def cpu_baseline(seconds: float):
-    return _oracle_sample(seconds)
+def cpu_baseline(seconds: float, single_seconds: float = 3.0):
+    """The oracle on all host cores, plus a single-thread figure on the next trajectories of the same
+    random order (about single_seconds of one core)."""
+    from oracle import oracle as O
+    cb = _oracle_sample(seconds)
+    if single_seconds > 0:
+        systems, y0, phi0, sid = batch(0, 4)
+        descs = [s.as_dict() for s in systems]
+        order = np.random.default_rng(12345).permutation(len(y0))[::-1]  # not the multi-thread sample
+        done, t_used, pos = 0, 0.0, 0
+        while t_used < single_seconds and pos < len(order):
+            idx = np.sort(order[pos:pos + 8])
+            pos += len(idx)
+            t0 = time.perf_counter()
+            O.run_batch(descs, y0[idx], phi0[idx], sid[idx], nthreads=1)
+            t_used += time.perf_counter() - t0
+            done += len(idx)
+        cb["single_thread"] = {"value": done / t_used, "unit": UNIT, "trajectories": done, "seconds": t_used}
+    return cb
 
 
 def run_reference(args, rank, world):
