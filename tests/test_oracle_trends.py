@@ -1,0 +1,42 @@
+"""Qualitative claims of the paper checked on the oracle (CPU only). These are sanity checks of the
+method as implemented, not parity: the paper prints no numbers for them.
+
+Fig. 1 discussion, on the Yb+-Rb head-on map at 1.5 uK:
+- there is a regular region where the atom leaves after a single bounce;
+- the line phi = pi/4 is dominated by complexes. There x = y, so the micromotion that q_x = -q_y
+  drives is perpendicular to the incoming velocity.
+
+Near the z axis the trap has no rf component (q_z = 0), so atoms arriving there meet no micromotion
+and leave after one bounce.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2509_15117_gb300 import inputs as I
+
+
+@pytest.fixture(scope="module")
+def maps():
+    systems, y0, phi0, sid = I.c1_workload(32)
+    descs = [s.as_dict() for s in systems]
+    out = {}
+    for k in range(4):  # phases k pi/4; k + 4 is the mirror image phi -> pi/2 - phi
+        r = O.run_batch(descs, y0, np.full(len(phi0), k * math.pi / 4), sid)
+        out[k] = r["n_bounce"].reshape(32, 32)  # [theta index, phi index]
+    return out
+
+
+def test_phi_quarter_pi_line_is_complex_dominated(maps):
+    for k, nb in maps.items():
+        cx = nb >= 2
+        diag = cx[:, 15:17].mean()  # the two phi columns that bracket pi/4
+        assert diag > 0.5 and diag > cx.mean(), (k, diag, cx.mean())
+
+
+def test_regular_region_and_the_z_axis(maps):
+    for k, nb in maps.items():
+        assert np.mean(nb == 1) > 0.3, k
+        assert np.all(nb[:3] == 1), k  # theta < 0.13 rad: within 7 degrees of the z axis
