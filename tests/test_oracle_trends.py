@@ -8,6 +8,8 @@ Fig. 1 discussion, on the Yb+-Rb head-on map at 1.5 uK:
 
 Near the z axis the trap has no rf component (q_z = 0), so atoms arriving there meet no micromotion
 and leave after one bounce.
+
+Fig. 4 inset: with Omega fixed, the complex probability rises with q_x.
 """
 import math
 
@@ -40,3 +42,16 @@ def test_regular_region_and_the_z_axis(maps):
     for k, nb in maps.items():
         assert np.mean(nb == 1) > 0.3, k
         assert np.all(nb[:3] == 1), k  # theta < 0.13 rad: within 7 degrees of the z axis
+
+
+def test_complex_probability_rises_with_q():
+    """Fig. 4 inset: for Yb+-Li at fixed Omega, raising q_x raises the complex probability. Head-on at
+    0.3 uK (near Li's threshold), r0 = 20,000 a0, random rf phase, 600 trajectories per q drawn by the
+    oracle's sampler."""
+    p = []
+    for q in (0.05, 0.1, 0.2, 0.3):
+        d = I.make_system("Li", q=q, r0=20000.0, E_K=0.3e-6, t_max_s=3e-3).as_dict()
+        y, ph = O.sample_ics(O.make_sampler(O.SAMPLE_HEAD_ON, d, 77, E=I.kelvin(0.3e-6)), 0, 600)
+        p.append(float(np.mean(O.run_batch([d], y, ph)["n_bounce"] >= 2)))
+    assert all(a < b for a, b in zip(p, p[1:])), p
+    assert p[0] < 0.1 < 0.2 < p[-1], p
