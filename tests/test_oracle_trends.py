@@ -10,6 +10,7 @@ Near the z axis the trap has no rf component (q_z = 0), so atoms arriving there 
 and leave after one bounce.
 
 Fig. 4 inset: with Omega fixed, the complex probability rises with q_x.
+Fig. 4 discussion: a fixed initial rf phase makes the complex probability oscillate with energy.
 """
 import math
 
@@ -55,3 +56,27 @@ def test_complex_probability_rises_with_q():
         p.append(float(np.mean(O.run_batch([d], y, ph)["n_bounce"] >= 2)))
     assert all(a < b for a, b in zip(p, p[1:])), p
     assert p[0] < 0.1 < 0.2 < p[-1], p
+
+
+def test_fixed_rf_phase_makes_p_oscillate_with_energy():
+    """Fig. 4 discussion: with a fixed initial rf phase the complex probability oscillates by about
+    +-0.1 as the energy varies (the phase at impact moves with the approach time r0/v0); a random
+    phase averages the oscillation out. Yb+-Li, q = 0.1, r0 = 20,000 a0, 12 energies over
+    0.25-0.35 uK, 300 trajectories each; the residual about a linear trend is compared with the
+    binomial noise."""
+    Es = np.linspace(0.25, 0.35, 12)
+    resid_std = {}
+    for rand in (False, True):
+        P = []
+        for E_uK in Es:
+            d = I.make_system("Li", q=0.1, r0=20000.0, E_K=E_uK * 1e-6, t_max_s=3e-3).as_dict()
+            smp = O.make_sampler(O.SAMPLE_HEAD_ON, d, 78, E=I.kelvin(E_uK * 1e-6), random_phase=rand, phase=0.0)
+            y, ph = O.sample_ics(smp, 0, 300)
+            P.append(float(np.mean(O.run_batch([d], y, ph)["n_bounce"] >= 2)))
+        P = np.array(P)
+        resid = P - np.polyval(np.polyfit(Es, P, 1), Es)
+        binom = math.sqrt(float(np.mean(P * (1 - P))) / 300)
+        resid_std[rand] = (float(resid.std()), binom, float(np.ptp(resid)))
+    fixed, rnd = resid_std[False], resid_std[True]
+    assert fixed[0] > 3 * fixed[1] and fixed[2] > 0.15, resid_std
+    assert rnd[0] < 1.5 * rnd[1], resid_std
