@@ -136,8 +136,11 @@ typedef struct ia_launch_opts {
 /*
  * Create a table of n_sys systems on the current CUDA device (copied to device memory).
  * Validation per row: masses, Omega, r0, t_max, tolerances, h_max > 0; alpha >= 0; De > 0 when
- * alpha > 0; rf_sign = +-1; max_attempts > 0; reserved = 0. Returns IA_ERR_BAD_DESC on failure and
- * writes nothing to *out. n_sys must be 1..65536.
+ * alpha > 0; rf_sign = +-1; max_attempts > 0; reserved = 0; |a_j|, |q_j| <= 16, and every axis
+ * Mathieu-stable: with tau = (Omega t + phi0)/2, Eq. 1 gives x'' + (a_j + 2 q_j cos 2 tau) x = 0 per
+ * axis, whose monodromy matrix over one rf period must have a trace within [-2, 2] (to 1e-8; the free
+ * axis a_j = q_j = 0 has trace 2 and is accepted). Returns IA_ERR_BAD_DESC on failure and writes
+ * nothing to *out. The checks run before any CUDA call. n_sys must be 1..65536.
  * Derived constants (text after Eq. 1): C4 = alpha/2, C8 = C4^2/(4 De).
  */
 int ia_system_create(const ia_system_desc* desc, int32_t n_sys, ia_system** out);

@@ -21,7 +21,10 @@
 #include <cstring>
 #include <cmath>
 #include <mutex>
+#include <map>
 #include <new>
+#include <utility>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "ia_traj.cuh"
@@ -1262,6 +1265,49 @@ int sample_device(int* sms)
     return (major == 10 && minor == 3 && *sms > 0) ? IA_OK : IA_ERR_NO_DEVICE;
 }
 
+// Stability of one trap axis. With tau = (Omega t + phi0)/2 the ion's equation of motion along axis j
+// (Eq. 1) is x'' + (a_j + 2 q_j cos 2 tau) x = 0, Mathieu's equation, whose solutions stay bounded when
+// the trace of the monodromy matrix over one rf period (tau from 0 to pi) lies within [-2, 2]
+// (Floquet). The trace is that of the two fundamental solutions, integrated with classical RK4 over
+// 4096 steps (error ~1e-12 for |a|, |q| <= 1). An axis with a = q = 0 has trace exactly 2 (free
+// motion: bounded velocity) and is accepted, as is any trace within 1e-8 of +-2.
+constexpr int kMathieuSteps = 4096;
+
+double mathieu_trace(double a, double q)
+{
+    static const std::vector<double> cos2 = [] {
+        std::vector<double> c(2 * kMathieuSteps + 1);
+        const double pi = 3.14159265358979323846;
+        for (int i = 0; i <= 2 * kMathieuSteps; ++i)
+            c[i] = std::cos(2.0 * (pi * (double)i / (2.0 * kMathieuSteps)));
+        return c;
+    }();
+    const double h = 3.14159265358979323846 / kMathieuSteps;
+    double tr = 0.0;
+    for (int sol = 0; sol < 2; ++sol) {
+        double x = sol == 0 ? 1.0 : 0.0, v = sol == 0 ? 0.0 : 1.0;
+        for (int i = 0; i < kMathieuSteps; ++i) {
+            const double w0 = a + 2.0 * q * cos2[2 * i];
+            const double wm = a + 2.0 * q * cos2[2 * i + 1];
+            const double w1 = a + 2.0 * q * cos2[2 * i + 2];
+            const double k1x = v, k1v = -w0 * x;
+            const double k2x = v + 0.5 * h * k1v, k2v = -wm * (x + 0.5 * h * k1x);
+            const double k3x = v + 0.5 * h * k2v, k3v = -wm * (x + 0.5 * h * k2x);
+            const double k4x = v + h * k3v, k4v = -w1 * (x + h * k3x);
+            x += h / 6.0 * (k1x + 2.0 * k2x + 2.0 * k3x + k4x);
+            v += h / 6.0 * (k1v + 2.0 * k2v + 2.0 * k3v + k4v);
+        }
+        tr += sol == 0 ? x : v;
+    }
+    return tr;
+}
+
+bool mathieu_stable(double a, double q)
+{
+    const double tr = mathieu_trace(a, q);
+    return std::isfinite(tr) && std::fabs(tr) <= 2.0 + 1e-8;
+}
+
 bool valid_desc(const ia_system_desc& d)
 {
     auto pos = [](double x) { return std::isfinite(x) && x > 0.0; };
@@ -1273,6 +1319,23 @@ bool valid_desc(const ia_system_desc& d)
         if (!std::isfinite(d.a[j]) || !std::isfinite(d.q[j])) return false;
     if (d.rf_sign != 1 && d.rf_sign != -1) return false;
     if (d.reserved != 0 || d.max_attempts <= 0 || d.max_attempts > 0x7fffffffLL) return false;
+    for (int j = 0; j < 3; ++j)
+        if (std::fabs(d.a[j]) > 16.0 || std::fabs(d.q[j]) > 16.0) return false;
+    return true;
+}
+
+// Every axis of every row Mathieu-stable; each distinct (a, |q|) pair is integrated once (the sign of
+// q shifts the rf phase by half a period and leaves the stability unchanged).
+bool stable_traps(const ia_system_desc* desc, int n_sys)
+{
+    std::map<std::pair<double, double>, bool> seen;
+    for (int k = 0; k < n_sys; ++k)
+        for (int j = 0; j < 3; ++j) {
+            const std::pair<double, double> key(desc[k].a[j], std::fabs(desc[k].q[j]));
+            auto it = seen.find(key);
+            if (it == seen.end()) it = seen.emplace(key, mathieu_stable(key.first, key.second)).first;
+            if (!it->second) return false;
+        }
     return true;
 }
 
@@ -1399,6 +1462,7 @@ int ia_system_create(const ia_system_desc* desc, int32_t n_sys, ia_system** out)
     if (!desc || !out || n_sys < 1 || n_sys > 65536) return IA_ERR_INVALID_ARG;
     for (int k = 0; k < n_sys; ++k)
         if (!valid_desc(desc[k])) return IA_ERR_BAD_DESC;
+    if (!stable_traps(desc, n_sys)) return IA_ERR_BAD_DESC;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return IA_ERR_NO_DEVICE;
     cudaDeviceProp prop;
