@@ -1,0 +1,63 @@
+"""Host-side logic that both sides rely on (CPU only): the workload builders, the differentiation
+seeds and the queue order."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2509_15117_gb300 import inputs as I
+from paper_2509_15117_gb300 import schedule as Sch
+
+
+def test_splitmix64_published_sequence():
+    """splitmix64 (Steele, Lea & Flood 2014) seeded with 0 outputs e220a8397b1dcdaf, 6e789e6aa1b965f4,
+    06c45d188009454f: the finaliser applied to 1, 2, 3 times the golden-ratio increment."""
+    gamma = 0x9E3779B97F4A7C15
+    want = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    for k, w in enumerate(want):
+        assert I.splitmix64((k * gamma) % 2 ** 64) == w
+
+
+def test_mixed_sweep_cells():
+    cells = I.c4_cells()
+    assert len(cells) == 250
+    sizes = {c["n"] for c in cells}
+    assert sizes <= {4096 * 2 ** k for k in range(7)} and len(sizes) > 3
+    assert len({(c["De_K"], c["q"], c["a"], c["species"]) for c in cells}) == 250
+
+
+def test_octant_grid_is_cell_centred():
+    th, ph = I.octant_grid(4)
+    step = 0.5 * math.pi / 4
+    assert np.allclose(np.unique(th), (np.arange(4) + 0.5) * step)
+    assert np.allclose(ph[:4], (np.arange(4) + 0.5) * step)  # phi fastest
+
+
+def test_head_on_seeds_are_the_derivatives_of_the_initial_state():
+    """d y0 / d(theta, phi, E) against central differences of head_on: the seeds feed both the tangent
+    kernel and the oracle's tangent, so parity between them cannot catch a wrong seed."""
+    d = I.make_system("Rb").as_dict()
+    E = I.kelvin(1.5e-6)
+    th, ph = np.array([0.3, 1.2]), np.array([0.7, 0.1])
+    m = d["m_atom"]
+    seeds = I.head_on_seeds(th, ph, d["r0"], math.sqrt(2 * E / m), E)
+
+    def state(t, p, e):
+        return I.head_on(t, p, d["r0"], math.sqrt(2 * e / m))
+
+    for k, (dt, dp, de) in enumerate([(1e-6, 0, 0), (0, 1e-6, 0), (0, 0, 1e-6 * E)]):
+        fd = (state(th + dt, ph + dp, E + de) - state(th - dt, ph - dp, E - de)) / (2 * (dt + dp + de))
+        scale = np.abs(seeds[:, k]).max(axis=1, keepdims=True)
+        assert np.all(np.abs(fd - seeds[:, k]) <= 1e-8 * scale), k
+    assert np.array_equal(I.q_direction(), [1.0, -1.0, 0.0])
+
+
+def test_queue_order_puts_costly_systems_first_and_keeps_the_rest_stable():
+    systems = [I.make_system(sp, E_K=1e-6) for sp in ("Li", "Cs", "Rb")]
+    speeds = [s.atol_vel / 1e-10 for s in systems]
+    cost = Sch.system_cost(systems, speeds)
+    assert cost[1] > cost[2] > cost[0]  # heavy and slow first
+    sid = np.array([0, 1, 2, 1, 0, 2, 1], dtype=np.int32)
+    order = Sch.order_by_cost(sid, cost)
+    assert sorted(order) == list(range(7))
+    assert list(order) == [1, 3, 6, 2, 5, 0, 4]
