@@ -61,3 +61,54 @@ def test_queue_order_puts_costly_systems_first_and_keeps_the_rest_stable():
     order = Sch.order_by_cost(sid, cost)
     assert sorted(order) == list(range(7))
     assert list(order) == [1, 3, 6, 2, 5, 0, 4]
+
+
+stats = pytest.importorskip("scipy.stats")
+
+
+def ks_ok(x, dist, *args):
+    return stats.kstest(x, dist, args=args).pvalue > 1e-4
+
+
+def test_host_thermal_samplers_follow_the_paper():
+    """The numpy samplers that feed both sides: atom on the r0 sphere with Gaussian velocity flipped
+    inward (thermal-runs paragraph), the disk variant, the ion Gaussian in the secular trap."""
+    vth = math.sqrt(I.kelvin(1e-4) / (I.SPECIES["Rb"]["mass_amu"] * I.AMU_TO_ME))
+    sysd = I.make_system("Rb", v_scale=vth)
+    n = 100_000
+    sig = math.sqrt(I.kelvin(1e-4) / sysd.m_atom)
+    y, ph = I.thermal_sphere(n, 1, sysd, 1e-4)
+    xh = y[:, 6:9] / sysd.r0
+    assert np.allclose(np.linalg.norm(xh, axis=1), 1.0, atol=1e-14)
+    assert ks_ok(xh[:, 2], "uniform", -1.0, 2.0)
+    vr = np.sum(y[:, 9:12] * xh, axis=1)
+    assert np.all(vr <= 0.0) and ks_ok(-vr / sig, "halfnorm")
+    assert ks_ok(np.sum(y[:, 9:12] ** 2, axis=1) / sig ** 2, "chi2", 3)
+    w = I.secular_omega(0.1, sysd.Omega)
+    sv = math.sqrt(I.kelvin(10e-6) / sysd.m_ion)
+    assert ks_ok(y[:, 0] / (sv / w), "norm") and ks_ok(y[:, 4] / sv, "norm")
+    assert ks_ok(ph, "uniform", 0.0, 2 * math.pi)
+    yd, _ = I.thermal_disk(n, 2, sysd, 1e-4)
+    vh = yd[:, 9:12] / np.linalg.norm(yd[:, 9:12], axis=1, keepdims=True)
+    along = np.sum(yd[:, 6:9] * vh, axis=1)
+    b = np.linalg.norm(yd[:, 6:9] - along[:, None] * vh, axis=1)
+    assert np.allclose(np.linalg.norm(yd[:, 6:9], axis=1), sysd.r0, rtol=1e-12)
+    assert ks_ok((b / 2000.0) ** 2, "uniform", 0.0, 1.0)
+    cth, phi = I.octant_random(n, 3)
+    assert ks_ok(np.cos(cth), "uniform", 0.0, 1.0) and ks_ok(phi, "uniform", 0.0, 0.5 * math.pi)
+
+
+def test_host_micromotion_covariance():
+    """thermal_ion at a fixed phase: cov(x_j, v_j) = -s (q_j Omega / 2) sin(phi0) (1 + s q_j/2 cos phi0)
+    sigma_X^2, the lowest-order Mathieu solution."""
+    sysd = I.make_system("Rb")
+    n = 200_000
+    ph = np.full(n, 0.5 * math.pi)
+    y = I.thermal_ion(n, np.random.default_rng(4), sysd.m_ion, 1e-5, sysd.q, sysd.Omega, ph)
+    sx = math.sqrt(I.kelvin(1e-5) / (sysd.m_ion * I.secular_omega(0.1, sysd.Omega) ** 2))
+    sv = math.sqrt(I.kelvin(1e-5) / sysd.m_ion)
+    for j in range(2):
+        k = 0.5 * sysd.q[j] * sysd.Omega
+        cov = np.mean(y[:, j] * y[:, 3 + j])
+        sd = math.sqrt(sv ** 2 + (k * sx) ** 2)
+        assert abs(cov - (-k * sx * sx)) < 5 * sx * sd / math.sqrt(n), j
