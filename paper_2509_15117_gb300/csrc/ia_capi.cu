@@ -1861,7 +1861,11 @@ int ia_launch_tangent(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_o
         !out->t_last_bounce || !out->n_bounce || !out->status || !out->n_steps || !out->n_rej)
         return IA_ERR_INVALID_ARG;
     if (out->y_final && out->ld < n) return IA_ERR_INVALID_ARG;
-    if (tin->ndir < 1 || tin->ndir > 4 || !tin->dy0 || tin->ld < n) return IA_ERR_INVALID_ARG;
+    if (!aligned8(ic->y0) || !aligned8(ic->phi0) || !aligned8(out->theta_s) || !aligned8(out->dp) ||
+        !aligned8(out->dE_ion) || !aligned8(out->t_final) || !aligned8(out->t_first_bounce) ||
+        !aligned8(out->t_last_bounce) || (out->y_final && !aligned8(out->y_final)))
+        return IA_ERR_ALIGNMENT;
+    if (tin->ndir < 1 || tin->ndir > 4 || !tin->dy0 || tin->ld < n || tin->reserved != 0) return IA_ERR_INVALID_ARG;
     if (!tout->d_theta_s || !tout->d_dp || !tout->d_dE_ion || !tout->d_t_final || tout->ld < n)
         return IA_ERR_INVALID_ARG;
     if (!aligned8(tin->dy0) || !aligned8(tout->d_theta_s) || !aligned8(tout->d_dp) || !aligned8(tout->d_dE_ion) ||
@@ -1889,7 +1893,7 @@ int ia_launch_tangent(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_o
     int resident = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_tangent, 128, 0) != cudaSuccess || resident <= 0)
         return IA_ERR_CUDA;
-    long long warps = (n + 0);
+    const long long warps = n;  // one warp per trajectory
     long long grid = (long long)resident * sys->num_sms;
     if (grid * 4 > warps) grid = (warps + 3) / 4;
     k_tangent<<<(unsigned)grid, 128, 0, st>>>(sys->d_tab, sys->n_sys, icp, op, (long long)n, ti, to, work);

@@ -145,3 +145,28 @@ def test_sampler_struct_and_argument_checks_without_gpu():
     assert L.ia_philox4x64(1, 2, 3, 0, 1, None, None) == -1
     assert L.ia_philox4x64(1, 2, 3, -1, 1, y, None) == -1
     assert L.ia_philox4x64(1, 2, 3, 0, 1, y + 4, None) == -4
+
+
+def test_tangent_entry_checks_alignment_and_reserved_without_gpu():
+    """ia_launch_tangent refuses misaligned pointers and a non-zero reserved field before touching the
+    system (a stand-in address that is never dereferenced on these paths)."""
+    L = Bd.load()
+    fake_sys = ctypes.c_void_p(0x2000)
+    n = 4
+    ic = Bd.ia_ic_soa(y0=0x10000, phi0=0x20000, sys_id=None, order=None, ld=n)
+    out = Bd.ia_obs_soa(*([0x30000 + 0x1000 * k for k in range(10)] + [None, 0]))
+    tin = Bd.ia_tangent_in(dy0=0x40000, ndir=1, reserved=0, ld=n)
+    tout = Bd.ia_tangent_out(d_theta_s=0x50000, d_dp=0x51000, d_dE_ion=0x52000, d_t_final=0x53000,
+                             dy_final=None, ftle=None, ld=n)
+    call = lambda: L.ia_launch_tangent(fake_sys, ctypes.byref(ic), n, ctypes.byref(out), ctypes.byref(tin),
+                                       ctypes.byref(tout), None)
+    ic.y0 = 0x10004
+    assert call() == -4
+    ic.y0 = 0x10000
+    out.dp = 0x31004
+    assert call() == -4
+    out.dp = 0x31000
+    tin.reserved = 1
+    assert call() == -1
+    tin.reserved, tin.ndir = 0, 5
+    assert call() == -1
