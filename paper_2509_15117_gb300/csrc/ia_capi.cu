@@ -1762,6 +1762,7 @@ int ia_autotune(ia_system* sys, const ia_ic_soa* ic, int64_t n, int32_t attempt_
     if (!sys || !ic || !best || !best_ms || n < 1 || attempt_cap < 64 || attempt_cap > (1 << 20))
         return IA_ERR_INVALID_ARG;
     if (!ic->y0 || !ic->phi0 || ic->ld < n) return IA_ERR_INVALID_ARG;
+    if (!aligned8(ic->y0) || !aligned8(ic->phi0) || (ic->order && !aligned8(ic->order))) return IA_ERR_ALIGNMENT;
     ia_launch_opts b0;
     std::memset(&b0, 0, sizeof(b0));
     if (base) b0 = *base;
@@ -2115,6 +2116,7 @@ int ia_rcp_check(const double* x, double* y, int64_t n, void* stream)
 {
     if (!x || !y || n < 0) return IA_ERR_INVALID_ARG;
     if (n == 0) return IA_OK;
+    if (!aligned8(x) || !aligned8(y)) return IA_ERR_ALIGNMENT;
     const long long blocks = (n + 255) / 256;
     k_rcp_check<<<(unsigned)blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, y, (long long)n);
     return cudaGetLastError() == cudaSuccess ? IA_OK : IA_ERR_CUDA;

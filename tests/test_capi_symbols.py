@@ -170,3 +170,16 @@ def test_tangent_entry_checks_alignment_and_reserved_without_gpu():
     assert call() == -1
     tin.reserved, tin.ndir = 0, 5
     assert call() == -1
+
+
+def test_autotune_and_rcp_hook_check_alignment_without_gpu():
+    L = Bd.load()
+    fake_sys = ctypes.c_void_p(0x2000)
+    ic = Bd.ia_ic_soa(y0=0x10004, phi0=0x20000, sys_id=None, order=None, ld=8)
+    best = Bd.ia_launch_opts()
+    ms = ctypes.c_double()
+    assert L.ia_autotune(fake_sys, ctypes.byref(ic), 8, 1024, None, ctypes.byref(best), ctypes.byref(ms), None) == -4
+    ic.y0, ic.order = 0x10000, 0x30004
+    assert L.ia_autotune(fake_sys, ctypes.byref(ic), 8, 1024, None, ctypes.byref(best), ctypes.byref(ms), None) == -4
+    assert L.ia_autotune(fake_sys, ctypes.byref(ic), 8, 32, None, ctypes.byref(best), ctypes.byref(ms), None) == -1
+    assert L.ia_rcp_check(ctypes.c_void_p(0x10004), ctypes.c_void_p(0x20000), 4, None) == -4
