@@ -193,6 +193,45 @@ static double spacing(double t)
 typedef int (*orc_accept_fn)(void* obs, double t_old, const double* y_old, double h,
                              const double* y_new, double k[7][ORC_N]);
 
+/* Constants of ode45's step-size rules (Shampine & Reichelt 1997). Macros so that a test can build
+ * the oracle with one of them changed and check that its pins catch the change. */
+#ifndef ORC_CTRL_SAFETY
+#define ORC_CTRL_SAFETY 1.25      /* growth: h / (ORC_CTRL_SAFETY err^ORC_CTRL_EXPONENT) */
+#endif
+#ifndef ORC_CTRL_EXPONENT
+#define ORC_CTRL_EXPONENT 0.2     /* 1/5: the local error of the pair behaves as h^5 */
+#endif
+#ifndef ORC_CTRL_GROW_MAX
+#define ORC_CTRL_GROW_MAX 5.0     /* largest growth of h after an accepted step */
+#endif
+#ifndef ORC_CTRL_SHRINK_SAFETY
+#define ORC_CTRL_SHRINK_SAFETY 0.8  /* first failure: h * max(floor, 0.8 err^(-1/5)) */
+#endif
+#ifndef ORC_CTRL_SHRINK_MIN
+#define ORC_CTRL_SHRINK_MIN 0.1   /* floor of that factor */
+#endif
+#ifndef ORC_CTRL_RETRY
+#define ORC_CTRL_RETRY 0.5        /* second and later failures of one step: h * 0.5 */
+#endif
+
+/* Optional record of every attempted step (test hook): start time, step size, error measure and
+ * whether it was accepted. */
+typedef struct {
+    int64_t cap, n;
+    double *t, *h, *err;
+    int32_t* acc;
+} orc_trace;
+
+static void trace_put(orc_trace* tr, double t, double h, double err, int acc)
+{
+    if (!tr || tr->n >= tr->cap) return;
+    tr->t[tr->n] = t;
+    tr->h[tr->n] = h;
+    tr->err[tr->n] = err;
+    tr->acc[tr->n] = acc;
+    tr->n += 1;
+}
+
 typedef struct {
     int64_t n_steps, n_rej;
     uint32_t status;
@@ -209,7 +248,7 @@ typedef struct {
  */
 static void dp5_drive(orc_rhs_fn rhs, const void* ctx, int n, double t0, double t_end, double* y,
                       double rtol, const double* atol, double hmax, double h0, int64_t max_attempts,
-                      orc_accept_fn on_accept, void* obs, orc_loop_state* st)
+                      orc_accept_fn on_accept, void* obs, orc_loop_state* st, orc_trace* tr)
 {
     double k[7][ORC_N], ynew[ORC_N], err[ORC_N];
     double t = t0;
@@ -244,6 +283,7 @@ static void dp5_drive(orc_rhs_fn rhs, const void* ctx, int n, double t0, double 
                 st->h_next = h;
                 return;
             }
+            trace_put(tr, t, h, errn, errn <= 1.0);
             if (errn <= 1.0) break;
             st->n_rej += 1;
             if (h <= hmin) {
@@ -254,9 +294,9 @@ static void dp5_drive(orc_rhs_fn rhs, const void* ctx, int n, double t0, double 
             }
             if (nofailed) {
                 nofailed = 0;
-                h = fmax(hmin, h * fmax(0.1, 0.8 * pow(errn, -0.2)));
+                h = fmax(hmin, h * fmax(ORC_CTRL_SHRINK_MIN, ORC_CTRL_SHRINK_SAFETY * pow(errn, -ORC_CTRL_EXPONENT)));
             } else {
-                h = fmax(hmin, 0.5 * h);
+                h = fmax(hmin, ORC_CTRL_RETRY * h);
             }
             if (st->n_steps + st->n_rej >= max_attempts) {
                 st->status |= ORC_MAX_STEPS;
@@ -275,11 +315,11 @@ static void dp5_drive(orc_rhs_fn rhs, const void* ctx, int n, double t0, double 
         t = t_new;
         if (stop) break;
         if (nofailed) {
-            double temp = 1.25 * pow(errn, 0.2);
-            if (temp > 0.2)
+            double temp = ORC_CTRL_SAFETY * pow(errn, ORC_CTRL_EXPONENT);
+            if (temp > 1.0 / ORC_CTRL_GROW_MAX)
                 h = h / temp;
             else
-                h = 5.0 * h;
+                h = ORC_CTRL_GROW_MAX * h;
         }
     }
     st->t = t;
@@ -454,7 +494,7 @@ void orc_trajectory(const orc_system* s, const double* y0, double phi0, orc_resu
     memcpy(y, y0, sizeof(y));
     orc_loop_state st;
     dp5_drive(ionatom_rhs, &o.ctx, ORC_N, 0.0, s->t_max, y, s->rtol, atol, s->h_max, 0.0,
-              s->max_attempts, ionatom_on_accept, &o, &st);
+              s->max_attempts, ionatom_on_accept, &o, &st, NULL);
 
     double t_f;
     if (o.exited) {
@@ -565,9 +605,25 @@ void orc_test_solve(int32_t kind, double p, double t_end, double rtol, double at
     double at[ORC_N];
     for (int i = 0; i < n; ++i) at[i] = atol;
     orc_loop_state st;
-    dp5_drive(test_rhs, &c, n, 0.0, t_end, y, rtol, at, hmax, 0.0, INT64_MAX, NULL, NULL, &st);
+    dp5_drive(test_rhs, &c, n, 0.0, t_end, y, rtol, at, hmax, 0.0, INT64_MAX, NULL, NULL, &st, NULL);
     *n_steps = st.n_steps;
     *n_rej = st.n_rej;
+}
+
+/* Adaptive solve of a test problem from t = 0 to t_end starting with step h0 (> 0; 0 = ode45's
+ * initial-step rule), recording every attempted step: start time, step size, error measure, accepted
+ * (at most cap records). Returns the number of records. y in/out. */
+int64_t orc_test_trace(int32_t kind, double p, double t_end, double rtol, double atol, double hmax, double h0,
+                       double* y, int64_t cap, double* t_out, double* h_out, double* err_out, int32_t* acc_out)
+{
+    test_ctx c = {kind, p};
+    int n = test_n(kind);
+    double at[ORC_N];
+    for (int i = 0; i < n; ++i) at[i] = atol;
+    orc_trace tr = {cap, 0, t_out, h_out, err_out, acc_out};
+    orc_loop_state st;
+    dp5_drive(test_rhs, &c, n, 0.0, t_end, y, rtol, at, hmax, h0, cap, NULL, NULL, &st, &tr);
+    return tr.n;
 }
 
 /* nsteps fixed steps of size h of a test problem; y in/out, err_out = last step's error estimate. */
@@ -624,7 +680,7 @@ void orc_ionatom_segment(const orc_system* s, double phi0, double t0, double t1,
         for (int j = 0; j < 3; ++j) atol[3 * b + j] = (b % 2 == 0) ? s->atol_pos : s->atol_vel;
     orc_loop_state st;
     dp5_drive(ionatom_rhs, &c, ORC_N, t0, t1, y, s->rtol, atol, s->h_max, 0.0, s->max_attempts,
-              NULL, NULL, &st);
+              NULL, NULL, &st, NULL);
     *n_steps = st.n_steps;
     *n_rej = st.n_rej;
 }
@@ -670,7 +726,7 @@ int64_t orc_trajectory_steps(const orc_system* s, const double* y0, double phi0,
     memcpy(y, y0, sizeof(y));
     orc_loop_state st;
     dp5_drive(ionatom_rhs, &so.o.ctx, ORC_N, 0.0, s->t_max, y, s->rtol, atol, s->h_max, 0.0,
-              s->max_attempts, record_on_accept, &so, &st);
+              s->max_attempts, record_on_accept, &so, &st, NULL);
     *mode = (so.o.exited && so.o.exit_flags == 0) ? 0 : 1;
     return so.n;
 }

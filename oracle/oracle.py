@@ -117,6 +117,7 @@ def lib():
         L.orc_test_solve.argtypes = [ctypes.c_int32, d, d, d, d, d, dp, P(ctypes.c_int64), P(ctypes.c_int64)]
         L.orc_test_fixed.argtypes = [ctypes.c_int32, d, d, ctypes.c_int64, dp, dp]
         L.orc_test_dense.argtypes = [ctypes.c_int32, d, d, d, dp, dp]
+        _trace_types(L)
         L.orc_ionatom_fixed.argtypes = [P(OrcSystem), d, d, d, ctypes.c_int64, dp]
         L.orc_ionatom_segment.argtypes = [P(OrcSystem), d, d, d, dp, P(ctypes.c_int64), P(ctypes.c_int64)]
         L.orc_max_threads.restype = ctypes.c_int32
@@ -216,6 +217,42 @@ def test_fixed(kind: int, p: float, h: float, nsteps: int, y0):
     err = np.zeros_like(y)
     lib().orc_test_fixed(kind, p, h, nsteps, _dptr(y), _dptr(err))
     return y, err
+
+
+def _trace_types(L):
+    d = ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.orc_test_trace.argtypes = [ctypes.c_int32, d, d, d, d, d, d, dp, ctypes.c_int64, dp, dp, dp,
+                                 ctypes.POINTER(ctypes.c_int32)]
+    L.orc_test_trace.restype = ctypes.c_int64
+
+
+def build_variant(defines: dict, workdir: str):
+    """A copy of the oracle compiled with some of its macros redefined (``{"ORC_CTRL_SAFETY": 0.9}``),
+    loaded from `workdir`: the tests plant a mistake in the oracle this way and check that its pins
+    catch it. Only the test-problem hooks are typed."""
+    tag = "_".join(f"{k}{v}" for k, v in sorted(defines.items())).replace(".", "p").replace("-", "m")
+    path = os.path.join(workdir, f"libia_oracle_{tag}.so")
+    flags = [f"-D{k}={v!r}" if not isinstance(v, str) else f"-D{k}={v}" for k, v in defines.items()]
+    subprocess.run(["gcc", *CFLAGS, *flags, "-o", path, *_SRCS, "-lm"], check=True)
+    L = ctypes.CDLL(path)
+    _trace_types(L)
+    return L
+
+
+def test_trace(kind: int, p: float, t_end: float, y0, rtol: float, atol: float, hmax: float, h0: float = 0.0,
+               cap: int = 100000, L=None):
+    """Every attempted step of an adaptive solve of a test problem: arrays t, h, err (the error measure)
+    and accepted, plus the final y. L: a variant library from build_variant (default: the oracle)."""
+    L = lib() if L is None else L
+    y = np.array(y0, dtype=np.float64)
+    t = np.zeros(cap)
+    h = np.zeros(cap)
+    e = np.zeros(cap)
+    acc = np.zeros(cap, dtype=np.int32)
+    m = L.orc_test_trace(kind, p, t_end, rtol, atol, hmax, h0, _dptr(y), cap, _dptr(t), _dptr(h), _dptr(e),
+                         acc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    return {"t": t[:m], "h": h[:m], "err": e[:m], "acc": acc[:m].astype(bool), "y": y}
 
 
 def test_dense(kind: int, p: float, h: float, s: float, y0):
