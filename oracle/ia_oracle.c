@@ -32,6 +32,7 @@
  * Compiled with -O2 -fno-fast-math -ffp-contract=off so every operation is one IEEE-754 double
  * operation in source order. OpenMP is used across trajectories only.
  */
+#define __STDC_WANT_IEC_60559_TYPES_EXT__ 1 /* _Float128 and its f128 functions */
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -222,6 +223,35 @@ typedef struct {
     int32_t* acc;
 } orc_trace;
 
+/* Rounding-noise model (test hook): after every accepted step each component moves by m ulps
+ * (nextafter, exact), m uniform on -ulps..ulps from a splitmix64 hash of (seed, trajectory, step,
+ * component). It stands for the accumulated effect of another rounding order at every step, to measure
+ * how far FP64 rounding alone moves a trajectory's observables. */
+typedef struct {
+    uint64_t seed, traj;
+    int32_t ulps;
+} orc_noise;
+
+/* splitmix64 (Steele, Lea & Flood, OOPSLA 2014): one output of the generator whose state is x. */
+static uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+static void noise_apply(const orc_noise* nz, int64_t step, int n, double* y)
+{
+    if (!nz || nz->ulps <= 0) return;
+    const uint64_t key = splitmix64(nz->seed ^ splitmix64(nz->traj));
+    for (int i = 0; i < n; ++i) {
+        const uint64_t r = splitmix64(key ^ ((uint64_t)step * 16u + (uint64_t)i));
+        const int m = (int)(r % (uint64_t)(2 * nz->ulps + 1)) - nz->ulps;
+        for (int u = 0; u < (m < 0 ? -m : m); ++u) y[i] = nextafter(y[i], m < 0 ? -INFINITY : INFINITY);
+    }
+}
+
 static void trace_put(orc_trace* tr, double t, double h, double err, int acc)
 {
     if (!tr || tr->n >= tr->cap) return;
@@ -248,7 +278,8 @@ typedef struct {
  */
 static void dp5_drive(orc_rhs_fn rhs, const void* ctx, int n, double t0, double t_end, double* y,
                       double rtol, const double* atol, double hmax, double h0, int64_t max_attempts,
-                      orc_accept_fn on_accept, void* obs, orc_loop_state* st, orc_trace* tr)
+                      orc_accept_fn on_accept, void* obs, orc_loop_state* st, orc_trace* tr,
+                      const orc_noise* nz)
 {
     double k[7][ORC_N], ynew[ORC_N], err[ORC_N];
     double t = t0;
@@ -314,6 +345,7 @@ static void dp5_drive(orc_rhs_fn rhs, const void* ctx, int n, double t0, double 
         }
         t = t_new;
         if (stop) break;
+        noise_apply(nz, st->n_steps, n, y);
         if (nofailed) {
             double temp = ORC_CTRL_SAFETY * pow(errn, ORC_CTRL_EXPONENT);
             if (temp > 1.0 / ORC_CTRL_GROW_MAX)
@@ -465,8 +497,8 @@ static int ionatom_on_accept(void* vobs, double t_old, const double* y_old, doub
     return 0;
 }
 
-/* Integrate one trajectory from y0 at t = 0 with rf phase phi0. */
-void orc_trajectory(const orc_system* s, const double* y0, double phi0, orc_result* r)
+/* Integrate one trajectory from y0 at t = 0 with rf phase phi0 (nz: rounding-noise model or NULL). */
+static void trajectory(const orc_system* s, const double* y0, double phi0, orc_result* r, const orc_noise* nz)
 {
     memset(r, 0, sizeof(*r));
     int ok = 1;
@@ -494,7 +526,7 @@ void orc_trajectory(const orc_system* s, const double* y0, double phi0, orc_resu
     memcpy(y, y0, sizeof(y));
     orc_loop_state st;
     dp5_drive(ionatom_rhs, &o.ctx, ORC_N, 0.0, s->t_max, y, s->rtol, atol, s->h_max, 0.0,
-              s->max_attempts, ionatom_on_accept, &o, &st, NULL);
+              s->max_attempts, ionatom_on_accept, &o, &st, NULL, nz);
 
     double t_f;
     if (o.exited) {
@@ -527,6 +559,11 @@ void orc_trajectory(const orc_system* s, const double* y0, double phi0, orc_resu
     r->dE_ion = ion_energy(s, phi0, t_f, r->y_final) - ion_energy(s, phi0, 0.0, y0);
 }
 
+void orc_trajectory(const orc_system* s, const double* y0, double phi0, orc_result* r)
+{
+    trajectory(s, y0, phi0, r, NULL);
+}
+
 /* Batch over n trajectories: y0 is n x 12 row-major; sys_id may be NULL (all system 0). */
 void orc_run_batch(const orc_system* systems, int32_t n_sys, const int32_t* sys_id,
                    const double* y0, const double* phi0, int64_t n, orc_result* out, int32_t nthreads)
@@ -543,6 +580,28 @@ void orc_run_batch(const orc_system* systems, int32_t n_sys, const int32_t* sys_
             continue;
         }
         orc_trajectory(&systems[sid], y0 + ORC_N * i, phi0[i], &out[i]);
+    }
+}
+
+/* The same batch under the rounding-noise model (test hook): trajectory i draws its noise from
+ * (seed, i), moving every component by up to `ulps` ulps after each accepted step. */
+void orc_run_batch_noise(const orc_system* systems, int32_t n_sys, const int32_t* sys_id, const double* y0,
+                         const double* phi0, int64_t n, orc_result* out, int32_t nthreads, uint64_t seed,
+                         int32_t ulps)
+{
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t sid = sys_id ? sys_id[i] : 0;
+        if (sid < 0 || sid >= n_sys) {
+            memset(&out[i], 0, sizeof(orc_result));
+            out[i].status = ORC_BAD_IC;
+            continue;
+        }
+        orc_noise nz = {seed, (uint64_t)i, ulps};
+        trajectory(&systems[sid], y0 + ORC_N * i, phi0[i], &out[i], &nz);
     }
 }
 
@@ -605,7 +664,7 @@ void orc_test_solve(int32_t kind, double p, double t_end, double rtol, double at
     double at[ORC_N];
     for (int i = 0; i < n; ++i) at[i] = atol;
     orc_loop_state st;
-    dp5_drive(test_rhs, &c, n, 0.0, t_end, y, rtol, at, hmax, 0.0, INT64_MAX, NULL, NULL, &st, NULL);
+    dp5_drive(test_rhs, &c, n, 0.0, t_end, y, rtol, at, hmax, 0.0, INT64_MAX, NULL, NULL, &st, NULL, NULL);
     *n_steps = st.n_steps;
     *n_rej = st.n_rej;
 }
@@ -622,7 +681,7 @@ int64_t orc_test_trace(int32_t kind, double p, double t_end, double rtol, double
     for (int i = 0; i < n; ++i) at[i] = atol;
     orc_trace tr = {cap, 0, t_out, h_out, err_out, acc_out};
     orc_loop_state st;
-    dp5_drive(test_rhs, &c, n, 0.0, t_end, y, rtol, at, hmax, h0, cap, NULL, NULL, &st, &tr);
+    dp5_drive(test_rhs, &c, n, 0.0, t_end, y, rtol, at, hmax, h0, cap, NULL, NULL, &st, &tr, NULL);
     return tr.n;
 }
 
@@ -680,7 +739,7 @@ void orc_ionatom_segment(const orc_system* s, double phi0, double t0, double t1,
         for (int j = 0; j < 3; ++j) atol[3 * b + j] = (b % 2 == 0) ? s->atol_pos : s->atol_vel;
     orc_loop_state st;
     dp5_drive(ionatom_rhs, &c, ORC_N, t0, t1, y, s->rtol, atol, s->h_max, 0.0, s->max_attempts,
-              NULL, NULL, &st, NULL);
+              NULL, NULL, &st, NULL, NULL);
     *n_steps = st.n_steps;
     *n_rej = st.n_rej;
 }
@@ -726,7 +785,7 @@ int64_t orc_trajectory_steps(const orc_system* s, const double* y0, double phi0,
     memcpy(y, y0, sizeof(y));
     orc_loop_state st;
     dp5_drive(ionatom_rhs, &so.o.ctx, ORC_N, 0.0, s->t_max, y, s->rtol, atol, s->h_max, 0.0,
-              s->max_attempts, record_on_accept, &so, &st, NULL);
+              s->max_attempts, record_on_accept, &so, &st, NULL, NULL);
     *mode = (so.o.exited && so.o.exit_flags == 0) ? 0 : 1;
     return so.n;
 }
@@ -977,93 +1036,97 @@ done:
 }
 
 /* ------------------------------------------------------------------------------------------ */
-/* The same frozen-step replay in long double (x86: 64-bit mantissa; aarch64: IEEE binary128).  */
-/* Rounding in FP64 is amplified ~10^7 by a bounce, which floors finite differences of the FP64  */
-/* replay near 1e-5; in extended precision they resolve the discrete derivative to ~1e-9.        */
+/* The same frozen-step replay in IEEE quad precision (_Float128, 113-bit mantissa, with glibc's    */
+/* f128 functions; the same format on x86-64 and aarch64). FP64 rounding is amplified ~10^7-10^8   */
+/* by a bounce, which floors finite differences of the FP64 replay near 1e-5 (and of an 80-bit      */
+/* replay near 1e-6 at 1.5 uK); in quad precision the rounding of the replay is ~1e-34 and the      */
+/* differences resolve the discrete derivative far below the FP64 tangent's own rounding.           */
 
-typedef long double ldbl;
+typedef _Float128 qreal;
 
-static void rhs_ld(const orc_system* s, const ldbl* qv, ldbl phi0, ldbl t, const ldbl* y, ldbl* f)
+
+static void rhs_q(const orc_system* s, const qreal* qv, qreal phi0, qreal t, const qreal* y, qreal* f)
 {
-    ldbl C4 = 0.5L * (ldbl)s->alpha;
-    ldbl C8 = C4 == 0.0L ? 0.0L : C4 * C4 / (4.0L * (ldbl)s->De);
-    ldbl d[3];
+    qreal C4 = (qreal)0.5 * (qreal)s->alpha;
+    qreal C8 = C4 == (qreal)0.0 ? (qreal)0.0 : C4 * C4 / ((qreal)4.0 * (qreal)s->De);
+    qreal d[3];
     for (int j = 0; j < 3; ++j) d[j] = y[6 + j] - y[j];
-    ldbl r = sqrtl(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    ldbl dVdr = -8.0L * C8 / powl(r, 9) + 4.0L * C4 / powl(r, 5);
-    ldbl Om = (ldbl)s->Omega;
-    ldbl cosv = (ldbl)s->rf_sign * cosl(Om * t + phi0);
+    qreal r = sqrtf128(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    qreal dVdr = (qreal)-8.0 * C8 / powf128(r, 9) + (qreal)4.0 * C4 / powf128(r, 5);
+    qreal Om = (qreal)s->Omega;
+    qreal cosv = (qreal)s->rf_sign * cosf128(Om * t + phi0);
     for (int j = 0; j < 3; ++j) {
-        ldbl Fa = -dVdr * d[j] / r;
-        ldbl Ft = -((ldbl)s->m_ion * Om * Om / 4.0L) * ((ldbl)s->a[j] + 2.0L * qv[j] * cosv) * y[j];
+        qreal Fa = -dVdr * d[j] / r;
+        qreal Ft = -((qreal)s->m_ion * Om * Om / (qreal)4.0) * ((qreal)s->a[j] + (qreal)2.0 * qv[j] * cosv) * y[j];
         f[0 + j] = y[3 + j];
-        f[3 + j] = (Ft - Fa) / (ldbl)s->m_ion;
+        f[3 + j] = (Ft - Fa) / (qreal)s->m_ion;
         f[6 + j] = y[9 + j];
-        f[9 + j] = Fa / (ldbl)s->m_atom;
+        f[9 + j] = Fa / (qreal)s->m_atom;
     }
 }
 
-static ldbl ion_energy_ld(const orc_system* s, const ldbl* qv, ldbl phi0, ldbl t, const ldbl* y)
+static qreal ion_energy_q(const orc_system* s, const qreal* qv, qreal phi0, qreal t, const qreal* y)
 {
-    ldbl Om = (ldbl)s->Omega;
-    ldbl cosv = (ldbl)s->rf_sign * cosl(Om * t + phi0);
-    ldbl E = 0.0L;
+    qreal Om = (qreal)s->Omega;
+    qreal cosv = (qreal)s->rf_sign * cosf128(Om * t + phi0);
+    qreal E = (qreal)0.0;
     for (int j = 0; j < 3; ++j) {
-        E += 0.5L * (ldbl)s->m_ion * y[3 + j] * y[3 + j];
-        E += ((ldbl)s->a[j] + 2.0L * qv[j] * cosv) * ((ldbl)s->m_ion * Om * Om / 8.0L) * y[j] * y[j];
+        E += (qreal)0.5 * (qreal)s->m_ion * y[3 + j] * y[3 + j];
+        E += ((qreal)s->a[j] + (qreal)2.0 * qv[j] * cosv) * ((qreal)s->m_ion * Om * Om / (qreal)8.0) * y[j] * y[j];
     }
     return E;
 }
 
-/* Replay from the initial state y0 + eps dy0 with q + eps dq, both formed in extended precision. */
-static void replay_ld(const orc_system* s, const double* y0d, const double* dy0, const double* dq, ldbl eps,
-                      double phi0d, const double* hs, int64_t nh, int32_t mode, double* obs)
+/* Replay from the initial state y0 + eps dy0 with q + eps dq, both formed in quad precision; the
+ * observables (theta_s, dp, dE_ion, t_final) in quad precision. */
+static void replay_q(const orc_system* s, const double* y0d, const double* dy0, const double* dq, qreal eps,
+                     double phi0d, const double* hs, int64_t nh, int32_t mode, qreal* obs)
 {
-    ldbl y[ORC_N], k[7][ORC_N], ys[ORC_N], y0[ORC_N], qv[3];
-    ldbl phi0 = (ldbl)phi0d;
-    for (int i = 0; i < ORC_N; ++i) y0[i] = y[i] = (ldbl)y0d[i] + eps * (ldbl)dy0[i];
-    for (int j = 0; j < 3; ++j) qv[j] = (ldbl)s->q[j] + eps * (ldbl)dq[j];
-    ldbl t = 0.0L;
-    ldbl yf[ORC_N];
-    ldbl tf = 0.0L;
+    qreal y[ORC_N], k[7][ORC_N], ys[ORC_N], y0[ORC_N], qv[3];
+    qreal phi0 = (qreal)phi0d;
+    for (int i = 0; i < ORC_N; ++i) y0[i] = y[i] = (qreal)y0d[i] + eps * (qreal)dy0[i];
+    for (int j = 0; j < 3; ++j) qv[j] = (qreal)s->q[j] + eps * (qreal)dq[j];
+    qreal t = (qreal)0.0;
+    qreal yf[ORC_N];
+    qreal tf = (qreal)0.0;
     for (int64_t m = 0; m < nh; ++m) {
-        ldbl h = (ldbl)hs[m];
-        rhs_ld(s, qv, phi0, t, y, k[0]);
+        qreal h = (qreal)hs[m];
+        rhs_q(s, qv, phi0, t, y, k[0]);
         for (int st = 1; st < 7; ++st) {
             for (int i = 0; i < ORC_N; ++i) {
-                ldbl acc = 0.0L;
-                for (int l = 0; l < st; ++l) acc += (ldbl)DP_A[st][l] * k[l][i];
+                qreal acc = (qreal)0.0;
+                for (int l = 0; l < st; ++l) acc += (qreal)DP_A[st][l] * k[l][i];
                 ys[i] = y[i] + h * acc;
             }
-            rhs_ld(s, qv, phi0, t + (ldbl)DP_C[st] * h, ys, k[st]);
+            rhs_q(s, qv, phi0, t + (qreal)DP_C[st] * h, ys, k[st]);
         }
         if (m == nh - 1 && mode == 0) {
-            ldbl lo = -0.5L, hi = 1.5L, r0sq = (ldbl)s->r0 * (ldbl)s->r0;
+            qreal lo = (qreal)-0.5, hi = (qreal)1.5, r0sq = (qreal)s->r0 * (qreal)s->r0;
             for (int it = 0; it < 400; ++it) {
-                ldbl mid = 0.5L * (lo + hi);
+                qreal mid = (qreal)0.5 * (lo + hi);
                 if (mid <= lo || mid >= hi) break;
-                ldbl d2 = 0.0L;
+                qreal d2 = (qreal)0.0;
                 for (int j = 0; j < 3; ++j) {
-                    ldbl pa = 0.0L, pi = 0.0L;
+                    qreal pa = (qreal)0.0, pi = (qreal)0.0;
                     for (int jj = 0; jj < 7; ++jj) {
-                        ldbl w = mid * ((ldbl)DP_BI[jj][0] + mid * ((ldbl)DP_BI[jj][1] + mid * ((ldbl)DP_BI[jj][2] +
-                                        mid * (ldbl)DP_BI[jj][3])));
+                        qreal w = mid * ((qreal)DP_BI[jj][0] + mid * ((qreal)DP_BI[jj][1] + mid * ((qreal)DP_BI[jj][2] +
+                                        mid * (qreal)DP_BI[jj][3])));
                         pa += w * k[jj][6 + j];
                         pi += w * k[jj][j];
                     }
-                    ldbl dj = (y[6 + j] + h * pa) - (y[j] + h * pi);
+                    qreal dj = (y[6 + j] + h * pa) - (y[j] + h * pi);
                     d2 += dj * dj;
                 }
-                if (d2 - r0sq < 0.0L)
+                if (d2 - r0sq < (qreal)0.0)
                     lo = mid;
                 else
                     hi = mid;
             }
             for (int i = 0; i < ORC_N; ++i) {
-                ldbl acc = 0.0L;
+                qreal acc = (qreal)0.0;
                 for (int jj = 0; jj < 7; ++jj) {
-                    ldbl w = hi * ((ldbl)DP_BI[jj][0] + hi * ((ldbl)DP_BI[jj][1] + hi * ((ldbl)DP_BI[jj][2] +
-                                   hi * (ldbl)DP_BI[jj][3])));
+                    qreal w = hi * ((qreal)DP_BI[jj][0] + hi * ((qreal)DP_BI[jj][1] + hi * ((qreal)DP_BI[jj][2] +
+                                   hi * (qreal)DP_BI[jj][3])));
                     acc += w * k[jj][i];
                 }
                 yf[i] = y[i] + h * acc;
@@ -1072,8 +1135,8 @@ static void replay_ld(const orc_system* s, const double* y0d, const double* dy0,
             goto done;
         }
         for (int i = 0; i < ORC_N; ++i) {
-            ldbl acc = 0.0L;
-            for (int l = 0; l < 7; ++l) acc += (ldbl)DP_B[l] * k[l][i];
+            qreal acc = (qreal)0.0;
+            for (int l = 0; l < 7; ++l) acc += (qreal)DP_B[l] * k[l][i];
             y[i] = y[i] + h * acc;
         }
         t = t + h;
@@ -1082,31 +1145,31 @@ static void replay_ld(const orc_system* s, const double* y0d, const double* dy0,
     tf = t;
 done:
     {
-        const ldbl* v0 = y0 + 9;
-        const ldbl* vf = yf + 9;
-        ldbl cr[3] = {v0[1] * vf[2] - v0[2] * vf[1], v0[2] * vf[0] - v0[0] * vf[2], v0[0] * vf[1] - v0[1] * vf[0]};
-        obs[0] = (double)atan2l(sqrtl(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]),
+        const qreal* v0 = y0 + 9;
+        const qreal* vf = yf + 9;
+        qreal cr[3] = {v0[1] * vf[2] - v0[2] * vf[1], v0[2] * vf[0] - v0[0] * vf[2], v0[0] * vf[1] - v0[1] * vf[0]};
+        obs[0] = atan2f128(sqrtf128(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]),
                                 v0[0] * vf[0] + v0[1] * vf[1] + v0[2] * vf[2]);
-        ldbl dv[3] = {vf[0] - v0[0], vf[1] - v0[1], vf[2] - v0[2]};
-        obs[1] = (double)((ldbl)s->m_atom * sqrtl(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]));
-        obs[2] = (double)(ion_energy_ld(s, qv, phi0, tf, yf) - ion_energy_ld(s, qv, phi0, 0.0L, y0));
-        obs[3] = (double)tf;
+        qreal dv[3] = {vf[0] - v0[0], vf[1] - v0[1], vf[2] - v0[2]};
+        obs[1] = (qreal)s->m_atom * sqrtf128(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+        obs[2] = ion_energy_q(s, qv, phi0, tf, yf) - ion_energy_q(s, qv, phi0, (qreal)0.0, y0);
+        obs[3] = tf;
     }
 }
 
-/* Central differences of the extended-precision replay along direction (dy0, dq), with the
- * perturbed initial state and q formed in extended precision; Richardson-combined spacings delta
- * and delta/2 (truncation O(delta^4)). out: derivatives of (theta_s, dp, dE_ion, t_final). */
+/* Central differences of the quad-precision replay along direction (dy0, dq), with the perturbed
+ * initial state and q formed in quad precision; Richardson-combined spacings delta and delta/2
+ * (truncation O(delta^4)), all in quad precision. out: derivatives of (theta_s, dp, dE_ion, t_final). */
 void orc_fd_ld(const orc_system* s, const double* y0, double phi0, const double* hs, int64_t nh, int32_t mode,
                const double* dy0, const double* dq, double delta, double* out)
 {
-    double D[2][4];
+    qreal D[2][4];
     for (int pass = 0; pass < 2; ++pass) {
-        double dl = pass == 0 ? delta : 0.5 * delta;
-        double op[4], om[4];
-        replay_ld(s, y0, dy0, dq, (ldbl)dl, phi0, hs, nh, mode, op);
-        replay_ld(s, y0, dy0, dq, -(ldbl)dl, phi0, hs, nh, mode, om);
-        for (int o = 0; o < 4; ++o) D[pass][o] = (op[o] - om[o]) / (2.0 * dl);
+        qreal dl = pass == 0 ? (qreal)delta : (qreal)0.5 * (qreal)delta;
+        qreal op[4], om[4];
+        replay_q(s, y0, dy0, dq, dl, phi0, hs, nh, mode, op);
+        replay_q(s, y0, dy0, dq, -dl, phi0, hs, nh, mode, om);
+        for (int o = 0; o < 4; ++o) D[pass][o] = (op[o] - om[o]) / ((qreal)2.0 * dl);
     }
-    for (int o = 0; o < 4; ++o) out[o] = (4.0 * D[1][o] - D[0][o]) / 3.0;
+    for (int o = 0; o < 4; ++o) out[o] = (double)(((qreal)4.0 * D[1][o] - D[0][o]) / (qreal)3.0);
 }

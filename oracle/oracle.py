@@ -110,6 +110,10 @@ def lib():
         L.orc_run_batch.argtypes = [P(OrcSystem), ctypes.c_int32, P(ctypes.c_int32), dp, dp,
                                     ctypes.c_int64, P(OrcResult), ctypes.c_int32]
         L.orc_run_batch.restype = None
+        L.orc_run_batch_noise.argtypes = [P(OrcSystem), ctypes.c_int32, P(ctypes.c_int32), dp, dp,
+                                          ctypes.c_int64, P(OrcResult), ctypes.c_int32, ctypes.c_uint64,
+                                          ctypes.c_int32]
+        L.orc_run_batch_noise.restype = None
         L.orc_potential.argtypes = [P(OrcSystem), d, dp, dp]
         L.orc_ionatom_rhs.argtypes = [P(OrcSystem), d, d, dp, dp]
         L.orc_ion_energy.argtypes = [P(OrcSystem), d, d, dp]
@@ -160,10 +164,13 @@ def max_threads() -> int:
     return int(lib().orc_max_threads())
 
 
-def run_batch(systems, y0, phi0, sys_id=None, nthreads: int = 0) -> np.ndarray:
+def run_batch(systems, y0, phi0, sys_id=None, nthreads: int = 0, noise_seed: int = 0,
+              noise_ulps: int = 0) -> np.ndarray:
     """Integrate every trajectory; returns a structured array with ``RESULT_DTYPE``.
 
     systems: list of descriptor dicts; y0: (n, 12) float64; phi0: (n,) float64; sys_id: (n,) int32.
+    noise_ulps > 0: under the rounding-noise model (every component moved by up to noise_ulps ulps after
+    each accepted step, drawn from noise_seed and the trajectory's position in the batch).
     """
     L = lib()
     y0 = np.ascontiguousarray(y0, dtype=np.float64)
@@ -177,8 +184,13 @@ def run_batch(systems, y0, phi0, sys_id=None, nthreads: int = 0) -> np.ndarray:
         assert sys_id.shape == (n,)
         sid_ptr = sys_id.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     out = np.zeros(n, dtype=RESULT_DTYPE)
-    L.orc_run_batch(arr, len(systems), sid_ptr, _dptr(y0), _dptr(phi0), n,
-                    out.ctypes.data_as(ctypes.POINTER(OrcResult)), int(nthreads))
+    if noise_ulps > 0:
+        L.orc_run_batch_noise(arr, len(systems), sid_ptr, _dptr(y0), _dptr(phi0), n,
+                              out.ctypes.data_as(ctypes.POINTER(OrcResult)), int(nthreads),
+                              int(noise_seed) & 0xFFFFFFFFFFFFFFFF, int(noise_ulps))
+    else:
+        L.orc_run_batch(arr, len(systems), sid_ptr, _dptr(y0), _dptr(phi0), n,
+                        out.ctypes.data_as(ctypes.POINTER(OrcResult)), int(nthreads))
     return out
 
 
