@@ -192,8 +192,10 @@ int ia_launch(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* 
  *     and 16128 suspend records); otherwise IA_ERR_TOO_LARGE and nothing runs. For large batches set
  *     opts->suspend_capacity <= 16128 (trajectories that find no record finish in their lanes).
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
- *     device current; make that first call before any stream capture. The current device must be the
- *     one the system table was created on (else IA_ERR_INVALID_ARG).
+ *     device current; make that first call before any stream capture. A device reset (cudaDeviceReset)
+ *     moves the array: the first call after it looks the address up again, so it too must come before
+ *     any capture. The current device must be the one the system table was created on (else
+ *     IA_ERR_INVALID_ARG).
  *   - Every call shares the one array and leaves its contents behind; the counters it needs at zero
  *     are cleared on the stream at the start of each call. Calls whose work overlaps on the GPU
  *     (other streams, other host threads) race on the array: serialise them.
@@ -201,6 +203,62 @@ int ia_launch(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* 
 #define IA_STATIC_SCRATCH_BYTES (4u << 20)
 int ia_launch_static(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* out,
                      const ia_launch_opts* opts, void* stream);
+
+/*
+ * ia_launch_phases for the allocation-free launch (no counterpart in the paper): the phase times and
+ * the count of bounded waits that ran out (*errors, if not NULL; 0 in a healthy run, otherwise some
+ * trajectories may have no result) of the last ia_launch_static on the current device, read from the
+ * library's fixed array. Synchronous (call it after that launch completed); allocates nothing.
+ * IA_ERR_INVALID_ARG if the current device is not the system's or the array holds no completed launch.
+ */
+int ia_static_phases(ia_system* sys, double* lane_ms, double* total_ms, int64_t* errors);
+
+/* ---- one batch integrated over several launches ---- */
+
+/*
+ * A work queue of one batch of n trajectories, integrated by a sequence of persistent launches
+ * ("parts"). Trajectory lengths in a batch are heavy-tailed: most atoms leave after one bounce,
+ * while complexes live up to the run's t_max (Fig. 2 passage: complexes alive past 600 us; the text
+ * after Eq. 1 puts the average at ~3e5 steps). A single launch over a large batch therefore lasts as
+ * long as its longest trajectory. A queue lets each launch do a bounded share of the batch instead:
+ *   - part k starts the next `count` queue positions (in ic->order, or 0..n-1);
+ *   - first it resumes, in lane mode, the trajectories the previous part left running;
+ *   - trajectories past opts->slice_budget attempted steps go to suspend records and run in group mode
+ *     on the reserved SMs, across parts, exactly as in ia_launch;
+ *   - a part that does not take the last queue positions ends as soon as its queue is exhausted: every
+ *     running trajectory is saved (lane mode: a carry record; group mode: a suspend record) and the
+ *     next part continues it where it stopped;
+ *   - the part that takes the last positions finishes every trajectory before it returns.
+ * Results are bit-identical to ia_launch (the plain kernel) whatever the split. A trajectory's
+ * observables are written by the part in which it ends; after the last part all n are written.
+ *
+ * ia_queue_create: fixes the launch options (kernel persistent; opts->scratch must be NULL and
+ *   opts->tail_pair not 1: the paired tail is not available here) and allocates the queue's device
+ *   scratch (cudaMalloc, synchronous): counters, suspend records as in ia_scratch_bytes(n, opts), and
+ *   two carry buffers of one 256-byte record per lane of the grid. Every block of the grid must be
+ *   resident (cooperative launch); otherwise IA_ERR_INVALID_ARG (a grid too large) or IA_ERR_NO_DEVICE.
+ *   n >= 1.
+ * ia_queue_launch: launches the next part on `stream` (asynchronous). ic and out describe the whole
+ *   batch (n trajectories, ld >= n) and must be the same arrays in every part of a batch (else
+ *   IA_ERR_INVALID_ARG); their contents may be written between parts (e.g. the inputs of the next
+ *   part's positions copied in), but the inputs of a trajectory that has started must not change until
+ *   its result is written. 0 <= count <= n - started; count = 0 continues the running trajectories
+ *   only. The part whose count reaches n is the last. A complete batch takes no further part until
+ *   ia_queue_reset. Parts of one queue must run in order on one stream (each reads what the previous
+ *   wrote).
+ * ia_queue_reset: starts a new batch of the same size and options (host state only; the next part
+ *   clears the device counters on its stream). No part of the queue may be in flight on another stream.
+ * ia_queue_state: queue positions started so far, parts launched, and n (any pointer may be NULL).
+ * ia_queue_phases: as ia_launch_phases, for the latest part (synchronous).
+ * ia_queue_destroy: frees the queue (NULL accepted); no part may be in flight.
+ */
+typedef struct ia_queue ia_queue; /* opaque */
+int ia_queue_create(ia_system* sys, int64_t n, const ia_launch_opts* opts, ia_queue** q);
+int ia_queue_launch(ia_queue* q, const ia_ic_soa* ic, const ia_obs_soa* out, int64_t count, void* stream);
+int ia_queue_reset(ia_queue* q);
+int ia_queue_state(const ia_queue* q, int64_t* started, int64_t* parts, int64_t* n);
+int ia_queue_phases(const ia_queue* q, double* lane_ms, double* total_ms, int64_t* errors);
+int ia_queue_destroy(ia_queue* q);
 
 /*
  * Phase times of the last persistent launch whose scratch is `scratch` (NULL: the system's own

@@ -33,7 +33,8 @@ EXPORTED = ("ia_system_create", "ia_system_destroy", "ia_system_count", "ia_scra
             "ia_launch", "ia_launch_static", "ia_reduce_stats", "ia_reserve_stats", "ia_graph_create",
             "ia_graph_launch", "ia_graph_destroy", "ia_autotune", "ia_launch_phases", "ia_launch_tangent",
             "ia_adjoint_scratch_bytes", "ia_launch_adjoint", "ia_philox4x64", "ia_sample_ics", "ia_fp64_peak",
-            "ia_rcp_check", "ia_error_string", "ia_version")
+            "ia_rcp_check", "ia_error_string", "ia_version", "ia_queue_create", "ia_queue_launch",
+            "ia_queue_reset", "ia_queue_state", "ia_queue_phases", "ia_queue_destroy", "ia_static_phases")
 
 IA_SAMPLE_HEAD_ON = 0
 IA_SAMPLE_SPHERE = 1
@@ -247,6 +248,20 @@ def load(build_if_missing: bool = True):
     L.ia_sample_ics.restype = ctypes.c_int
     L.ia_fp64_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, P(ctypes.c_double)]
     L.ia_fp64_peak.restype = ctypes.c_int
+    L.ia_static_phases.argtypes = [ctypes.c_void_p, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int64)]
+    L.ia_static_phases.restype = ctypes.c_int
+    L.ia_queue_create.argtypes = [ctypes.c_void_p, ctypes.c_int64, P(ia_launch_opts), P(ctypes.c_void_p)]
+    L.ia_queue_create.restype = ctypes.c_int
+    L.ia_queue_launch.argtypes = [ctypes.c_void_p, P(ia_ic_soa), P(ia_obs_soa), ctypes.c_int64, ctypes.c_void_p]
+    L.ia_queue_launch.restype = ctypes.c_int
+    L.ia_queue_reset.argtypes = [ctypes.c_void_p]
+    L.ia_queue_reset.restype = ctypes.c_int
+    L.ia_queue_state.argtypes = [ctypes.c_void_p, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)]
+    L.ia_queue_state.restype = ctypes.c_int
+    L.ia_queue_phases.argtypes = [ctypes.c_void_p, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int64)]
+    L.ia_queue_phases.restype = ctypes.c_int
+    L.ia_queue_destroy.argtypes = [ctypes.c_void_p]
+    L.ia_queue_destroy.restype = ctypes.c_int
     L.ia_error_string.argtypes = [ctypes.c_int]
     L.ia_error_string.restype = ctypes.c_char_p
     L.ia_version.restype = ctypes.c_int
@@ -463,6 +478,14 @@ def ia_launch_static(handle: int, y0_soa, phi0, sys_id, out: dict, stream=None, 
     opts = make_opts(kernel=IA_KERNEL_PERSISTENT, **kw)
     _check(load().ia_launch_static(handle, ctypes.byref(ic), n, ctypes.byref(o), ctypes.byref(opts),
                                    _stream_ptr(stream)))
+
+
+def ia_static_phases(handle: int) -> tuple:
+    """(lane-phase ms, total ms, bounded waits that ran out) of the last ia_launch_static on the current
+    device, read from the library's fixed array; synchronous."""
+    a, b, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _check(load().ia_static_phases(handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(e)))
+    return a.value, b.value, e.value
 
 
 def alloc_stats(n_cells: int, device="cuda"):
@@ -686,6 +709,62 @@ def ia_launch_adjoint(handle: int, y0_soa, phi0, sys_id, out: dict, adj: dict, d
     _check(load().ia_launch_adjoint(handle, ctypes.byref(ic), n, ctypes.byref(o),
                                     ctypes.byref(ti) if ti is not None else None, ctypes.byref(ao),
                                     ctypes.byref(op), _stream_ptr(stream)))
+
+
+class Queue:
+    """Work queue of one batch of n trajectories integrated over several launches (ia_queue_*).
+
+    Each launch() starts the next `count` queue positions and continues what earlier parts left
+    running; the part whose count reaches n finishes the batch. The tensors (the whole batch) must be
+    the same in every part of a batch."""
+
+    def __init__(self, handle: int, n: int, **kw):
+        self.ptr = None
+        self.n = int(n)
+        opts = make_opts(kernel=IA_KERNEL_PERSISTENT, **kw)
+        q = ctypes.c_void_p()
+        _check(load().ia_queue_create(handle, self.n, ctypes.byref(opts), ctypes.byref(q)))
+        self.ptr = q.value
+
+    def launch(self, y0_soa, phi0, sys_id, out: dict, count: int, order=None, stream=None) -> None:
+        n = int(phi0.shape[0])
+        if n != self.n:
+            raise IaArgumentError(f"phi0: {n} trajectories, the queue holds {self.n}")
+        ic = _ic_struct(y0_soa, phi0, sys_id, order)
+        o = _obs_struct(out, n)
+        _check(load().ia_queue_launch(self.ptr, ctypes.byref(ic), ctypes.byref(o), int(count), _stream_ptr(stream)))
+
+    def reset(self) -> None:
+        _check(load().ia_queue_reset(self.ptr))
+
+    def state(self) -> tuple:
+        """(positions started, parts launched, n)."""
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().ia_queue_state(self.ptr, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def phases(self) -> tuple:
+        """(lane-phase ms, total ms, bounded waits that ran out) of the latest part; synchronous."""
+        a, b, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        _check(load().ia_queue_phases(self.ptr, ctypes.byref(a), ctypes.byref(b), ctypes.byref(e)))
+        return a.value, b.value, e.value
+
+    def close(self) -> None:
+        if self.ptr:
+            _check(load().ia_queue_destroy(self.ptr))
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class System:

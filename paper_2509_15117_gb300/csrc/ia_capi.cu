@@ -16,6 +16,7 @@
 //   k_tail<G>     finishes records the fused kernel left (normally none).
 //   k_fp64_fma    FP64 FMA throughput microbenchmark: the denominator of the integrator's roofline.
 #include <algorithm>
+#include <cstddef>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -25,6 +26,7 @@
 #include <new>
 #include <utility>
 #include <vector>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "ia_traj.cuh"
@@ -39,20 +41,58 @@ using namespace ia;
 namespace {
 
 // Work counters at the start of the scratch area; suspend-record ready flags and the records follow.
+// The first group is cleared before every launch; the second holds the state a batch keeps between
+// the launches of an ia_queue (suspend records and lane-mode carry records), cleared when a batch
+// starts.
 struct Counters {
     unsigned long long work;        // next queue position for the lane phase
-    unsigned long long n_susp;      // suspend records taken by writers
-    unsigned long long tail;        // next suspend record to resume
     unsigned long long warps_done;  // warps that have left the lane phase
     unsigned long long errors;      // bounded waits that ran out (stays 0 in a healthy run)
     unsigned long long t_start;     // %globaltimer (ns) when the first block started
     unsigned long long t_lane_end;  // ... when the last warp left the lane phase
     unsigned long long t_end;       // ... when the last warp finished (fused and clean-up kernels)
     unsigned int sm_claim[192];     // blocks seen per SM, to give one block per reserved SM the tail role
+    unsigned long long tc_taken;    // group-mode carry records of the previous part claimed so far
+    // --- kept between the launches of one batch ---
+    unsigned long long n_susp;      // suspend records taken by writers
+    unsigned long long tail;        // next suspend record to resume
+    unsigned long long carry_n[2];  // lane-mode carry records written into buffer 0 / 1
+    unsigned long long tcarry_n[2]; // group-mode carry records written into buffer 0 / 1
 };
 constexpr size_t SCRATCH_HEAD = 1024;
 static_assert(sizeof(Counters) <= SCRATCH_HEAD, "scratch head");
+constexpr size_t PER_LAUNCH_BYTES = offsetof(Counters, n_susp);
+// a test of the suspend-record overflow reads these two counters from a caller's scratch
+static_assert(offsetof(Counters, errors) == 16 && offsetof(Counters, n_susp) == 824, "counter layout");
 constexpr int MAX_TAIL_SMS = 192;
+
+// The part of a batch one launch of the fused kernel works on. A single ia_launch is one part that
+// is also the last: it starts queue positions 0..n-1 and finishes everything. The launches of an
+// ia_queue split a batch into parts: each starts the next `count` queue positions after resuming,
+// in lane mode, the trajectories the previous part left running; a part that is not the last ends as
+// soon as its queue is exhausted, leaving its running lane-mode trajectories in carry records and its
+// running group-mode trajectories in suspend records for the next part.
+struct Part {
+    long long first;                        // queue position of the part's first new trajectory
+    long long count;                        // new trajectories of this part
+    const Susp* carry_in;                   // lane-mode trajectories left by the previous part
+    const unsigned long long* carry_in_n;   // how many (null: none)
+    Susp* carry_out;                        // where this part leaves its running lane-mode trajectories
+    unsigned long long* carry_out_n;
+    long long carry_cap;                    // records per carry buffer
+    const Susp* tcarry_in;                  // group-mode trajectories the previous part's tail was running:
+    const unsigned long long* tcarry_in_n;  //   resumed by this part's tail before any suspend record
+    Susp* tcarry_out;                       // where this part's tail leaves its running trajectories
+    unsigned long long* tcarry_out_n;
+    long long tcarry_cap;                   // records per group-mode carry buffer
+    int last;                               // 1: finish every trajectory (no carry out)
+    int lane_only;                          // 1: the lane phase alone (the autotuner's timing runs)
+};
+
+// Warps of a reserved SM's block that work on the tail: one per SM sub-partition, so that each tail
+// warp has an FP64 unit to itself (the latency of one trajectory in group mode is its FP64 instruction
+// count per step); further warps of that block leave.
+constexpr int TAIL_WARPS = 4;
 
 __device__ __forceinline__ unsigned long long global_ns()
 {
@@ -95,8 +135,13 @@ __global__ void __launch_bounds__(128) k_plain(const SysDev* __restrict__ tab, i
 // together with one atomic add; a trajectory that has used `budget` attempted steps is written to a
 // suspend record (published by its ready flag) and the lane takes new work. With one_batch the warp
 // claims once (32 positions) and returns when those are finished or suspended.
+// The part's queue has n_virt = n_carry + part.count positions: positions below n_carry resume the
+// carry records of the previous part, the others start trajectories part.first + (pos - n_carry) of
+// the batch's queue. When the part is not the last, every lane leaves its trajectory in a carry record
+// as soon as the queue is exhausted.
 __device__ __forceinline__ void lane_phase(const SysDev* __restrict__ tab, int n_sys, const IcPtrs& ic,
-                                           const ObsPtrs& out, long long n, Counters* __restrict__ ctr,
+                                           const ObsPtrs& out, const Part& part, long long n_virt,
+                                           long long n_carry, Counters* __restrict__ ctr,
                                            unsigned* __restrict__ ready, Susp* __restrict__ susp, long long cap,
                                            int refill, int budget, bool one_batch = false)
 {
@@ -107,7 +152,21 @@ __device__ __forceinline__ void lane_phase(const SysDev* __restrict__ tab, int n
     int sid = 0;
     bool can_suspend = false;
     bool drained = false;  // the queue has been seen empty by this warp
+    const bool may_carry = !part.last;
     for (;;) {
+        if (may_carry) {
+            const bool exhausted = *(volatile unsigned long long*)&ctr->work >= (unsigned long long)n_virt;
+            if (exhausted) {
+                drained = true;
+                if (my >= 0) {
+                    const unsigned long long slot = atomicAdd(part.carry_out_n, 1ull);
+                    if (slot < (unsigned long long)part.carry_cap) {
+                        lane_suspend(L, my, sid, part.carry_out + slot);
+                        my = -1;
+                    }  // else (not expected: a buffer holds every lane of the grid) the lane finishes it
+                }
+            }
+        }
         const unsigned idle = __ballot_sync(FULL, my < 0);
         const int n_idle = __popc(idle);
         if (!drained && (n_idle >= refill || n_idle == 32)) {
@@ -115,12 +174,16 @@ __device__ __forceinline__ void lane_phase(const SysDev* __restrict__ tab, int n
             if (lane == 0) base = atomicAdd(&ctr->work, (unsigned long long)n_idle);
             base = __shfl_sync(FULL, base, 0);
             // one_batch: a single claim of 32 positions, run to completion (a tail worker lending a hand)
-            if (one_batch || base + (unsigned long long)n_idle >= (unsigned long long)n) drained = true;
+            if (one_batch || base + (unsigned long long)n_idle >= (unsigned long long)n_virt) drained = true;
             if (my < 0) {
                 const int rank = __popc(idle & ((1u << lane) - 1u));
                 const unsigned long long pos = base + (unsigned long long)rank;
-                if (pos < (unsigned long long)n) {
-                    my = ic.order ? __ldg(ic.order + pos) : (long long)pos;
+                if (pos < (unsigned long long)n_carry) {
+                    lane_resume(part.carry_in + pos, L, my, sid);
+                    can_suspend = budget > 0;
+                } else if (pos < (unsigned long long)n_virt) {
+                    const long long qp = part.first + (long long)pos - n_carry;
+                    my = ic.order ? __ldg(ic.order + qp) : qp;
                     sid = ic.sys_id ? __ldg(ic.sys_id + my) : 0;
                     if (sid < 0 || sid >= n_sys) {
                         store_bad_sid(ic, out, tab, my);
@@ -184,11 +247,18 @@ __device__ __forceinline__ bool claim_record(Counters* ctr, long long cap, unsig
 // lane-phase queue (of length help_n) are left, so that its caller can run a batch of the lane phase
 // (the reserved SMs then add to the bulk whenever the tail queue is empty); otherwise returns 0 when
 // the tail is done.
+// may_yield (a part of an ia_queue batch that is not the last): once every warp has left the lane
+// phase, each group leaves its running trajectory in a new suspend record, published like the lane
+// phase's, and the worker returns 0; the next part's tail resumes those records.
+// The group-mode carry records of the previous part (part.tcarry_in, n_tc of them) are resumed before
+// any suspend record: they hold the trajectories that part's tail was running, the oldest in the tail.
+// A yield writes to part.tcarry_out, or, when that is full, appends a suspend record.
 template <int G>
 __device__ __forceinline__ int tail_phase(const SysDev* __restrict__ tab, const IcPtrs& ic, const ObsPtrs& out,
-                                          const Susp* __restrict__ susp, const unsigned* __restrict__ ready,
+                                          Susp* __restrict__ susp, unsigned* __restrict__ ready,
                                           Counters* __restrict__ ctr, long long cap, bool wait_ok,
-                                          unsigned long long total_warps, long long help_n = 0)
+                                          unsigned long long total_warps, const Part& part, long long n_tc,
+                                          long long help_n = 0, bool may_yield = false)
 {
     constexpr int R = (N_COEF + G - 1) / G;  // coefficient rounds per lane
     const GroupLane<G> gl = group_lane<G>();
@@ -201,7 +271,52 @@ __device__ __forceinline__ int tail_phase(const SysDev* __restrict__ tab, const 
     bool active = false, drained = false;
     unsigned idle_spins = 0;
     unsigned claim_skip = 0;  // iterations without a claim attempt while other groups of the warp run
+    bool yield_room = true;   // false once a yield found the record area full (warp-uniform)
     for (;;) {
+        bool stop = false;
+        if (may_yield && yield_room) {
+            unsigned long long wd = 0;
+            if ((threadIdx.x & 31) == 0) wd = *(volatile unsigned long long*)&ctr->warps_done;
+            stop = __shfl_sync(FULL, wd, 0) >= total_warps;
+        }
+        if (stop) {
+            unsigned long long slot = 0;
+            int dest = 0;  // 1: group-mode carry record, 2: suspend record, 0: no room
+            if (active && gl.c == 0) {
+                slot = part.tcarry_out ? atomicAdd(part.tcarry_out_n, 1ull) : ~0ull;
+                if (slot < (unsigned long long)part.tcarry_cap) {
+                    dest = 1;
+                } else {
+                    slot = atomicAdd(&ctr->n_susp, 1ull);
+                    dest = slot < (unsigned long long)cap ? 2 : 0;
+                }
+            }
+            slot = __shfl_sync(FULL, slot, gl.base);
+            dest = __shfl_sync(FULL, dest, gl.base);
+            const bool room = active && dest != 0;
+            if (room) {
+                Susp* r = (dest == 1 ? part.tcarry_out : susp) + slot;
+                if (gl.c < 6) {
+                    r->x[gl.comp] = x;
+                    r->v[gl.comp] = v;
+                    r->a1[gl.comp] = a1;
+                }
+                if (gl.c == 0) {
+                    r->t = S.t; r->h = S.h; r->phi0 = S.phi0; r->rdot_prev = S.rdot_prev;
+                    r->t_first = S.t_first; r->t_last = S.t_last;
+                    r->idx = idx; r->sid = sid;
+                    r->n_acc = S.n_acc; r->n_rej = S.n_rej; r->n_bounce = S.n_bounce;
+                    r->flags = (S.nofailed ? 1 : 0) | (S.retry ? 2 : 0);
+                }
+                __threadfence();
+            }
+            __syncwarp();
+            if (room && dest == 2 && gl.c == 0) atomicExch(ready + slot, 1u);
+            if (__any_sync(FULL, active && !room)) yield_room = false;  // no room (not expected): finish here
+            if (room) active = false;
+            drained = true;
+            if (!__any_sync(FULL, active)) return 0;
+        }
         const bool need = !active && !drained;
         bool poll = __any_sync(FULL, need);
         if (poll && claim_skip > 0 && __any_sync(FULL, active)) {
@@ -214,7 +329,12 @@ __device__ __forceinline__ int tail_phase(const SysDev* __restrict__ tab, const 
             // the group's first lane claims; the claim is broadcast to the group
             int got = 0;
             unsigned long long k = 0;
-            if (need && gl.c == 0) {
+            if (need && gl.c == 0 && n_tc > 0 &&
+                *(volatile unsigned long long*)&ctr->tc_taken < (unsigned long long)n_tc) {
+                k = atomicAdd(&ctr->tc_taken, 1ull);
+                if (k < (unsigned long long)n_tc) got = 4;  // a trajectory the previous part's tail ran
+            }
+            if (need && gl.c == 0 && got == 0) {
                 if (claim_record(ctr, cap, k)) {
                     got = 1;
                     unsigned spins = 0;
@@ -249,11 +369,11 @@ __device__ __forceinline__ int tail_phase(const SysDev* __restrict__ tab, const 
             }
             got = __shfl_sync(FULL, got, gl.base);
             k = __shfl_sync(FULL, k, gl.base);
-            if (!__any_sync(FULL, need && got == 1)) claim_skip = CLAIM_BACKOFF;
+            if (!__any_sync(FULL, need && (got == 1 || got == 4))) claim_skip = CLAIM_BACKOFF;
             if (need) {
-                if (got == 1) {
-                    // written by another SM during this launch: read through L2
-                    const Susp* r = susp + k;
+                if (got == 1 || got == 4) {
+                    // written by another SM during this launch (or by the previous launch): read through L2
+                    const Susp* r = (got == 4 ? part.tcarry_in : susp) + k;
                     x = __ldcg(&r->x[gl.comp]);
                     v = __ldcg(&r->v[gl.comp]);
                     a1 = __ldcg(&r->a1[gl.comp]);
@@ -838,10 +958,12 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
 // Fused persistent kernel. Blocks on SMs with id < tail_sms (one block per such SM) are tail
 // workers from the start, so long-lived complexes run in group mode on sub-partitions of their own
 // while the rest of the GPU works through the queue; every other block runs the lane phase and then
-// joins the tail phase.
+// joins the tail phase. In a part of a batch that is not the last, the lane-phase warps leave once the
+// part's queue is exhausted (their running trajectories go to carry records) and the tail workers
+// then leave theirs in suspend records: the next part continues both.
 template <int BLOCK, int MINB, int G>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sched(const SysDev* __restrict__ tab, int n_sys, IcPtrs ic,
-                                                       ObsPtrs out, long long n, Counters* __restrict__ ctr,
+                                                       ObsPtrs out, Part part, Counters* __restrict__ ctr,
                                                        unsigned* __restrict__ ready, Susp* __restrict__ susp,
                                                        long long cap, int refill, int budget, int tail_sms,
                                                        int wait_ok, int pair)
@@ -862,23 +984,44 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sched(const SysDev* __restrict_
         role = r;
     }
     __syncthreads();
-    const int r = role;
+    // a reserved SM's block keeps TAIL_WARPS tail warps; its other warps leave (pairs need all of them)
+    const int r = (role == 1 && !(G == 6 && pair && wait_ok) && (threadIdx.x >> 5) >= TAIL_WARPS) ? 2 : role;
     const unsigned long long total_warps = (unsigned long long)gridDim.x * (BLOCK / 32);
-    if (r == 0) lane_phase(tab, n_sys, ic, out, n, ctr, ready, susp, cap, refill, budget);
+    // carry records written by the previous part's launch (complete before this launch started)
+    long long n_carry = 0, n_tc = 0;
+    if (part.carry_in_n) {
+        const unsigned long long c = *part.carry_in_n;
+        n_carry = c < (unsigned long long)part.carry_cap ? (long long)c : part.carry_cap;
+    }
+    if (part.tcarry_in_n) {
+        const unsigned long long c = *part.tcarry_in_n;
+        n_tc = c < (unsigned long long)part.tcarry_cap ? (long long)c : part.tcarry_cap;
+    }
+    const long long n_virt = n_carry + part.count;
+    if (r == 0) lane_phase(tab, n_sys, ic, out, part, n_virt, n_carry, ctr, ready, susp, cap, refill, budget);
     if ((threadIdx.x & 31) == 0) {
         __threadfence();
         if (atomicAdd(&ctr->warps_done, 1ull) + 1ull == total_warps) atomicMax(&ctr->t_lane_end, global_ns());
     }
-    if (G == 6 && r == 1 && pair && wait_ok) {
+    if (part.lane_only) {
+        // timing runs of the lane phase: trajectories past the budget stay in their suspend records
+    } else if (!part.last) {
+        // only the reserved-SM workers stay: they work on the tail (and lend a hand to the lane phase)
+        // until every lane-phase warp has left, then leave their trajectories for the next part
+        if (r == 1 && budget > 0)
+            while (tail_phase<G>(tab, ic, out, susp, ready, ctr, cap, wait_ok != 0, total_warps, part, n_tc, n_virt,
+                                 true) == 1)
+                lane_phase(tab, n_sys, ic, out, part, n_virt, n_carry, ctr, ready, susp, cap, refill, budget, true);
+    } else if (G == 6 && r == 1 && pair && wait_ok) {
         // dedicated tail block: warps 2p and 2p+1 form pair p (chain and helper warp)
         const int w = threadIdx.x >> 5;
         tail_phase_pair(tab, ic, out, susp, ready, ctr, cap, total_warps, &pair_sh[G == 6 ? (w >> 1) : 0],
                         (w & 1) != 0);
     } else if (r != 2 && budget > 0) {
         // a reserved-SM worker that finds the tail queue empty runs batches of the lane phase meanwhile
-        const long long help_n = r == 1 ? n : 0;
-        while (tail_phase<G>(tab, ic, out, susp, ready, ctr, cap, wait_ok != 0, total_warps, help_n) == 1)
-            lane_phase(tab, n_sys, ic, out, n, ctr, ready, susp, cap, refill, budget, true);
+        const long long help_n = r == 1 ? n_virt : 0;
+        while (tail_phase<G>(tab, ic, out, susp, ready, ctr, cap, wait_ok != 0, total_warps, part, n_tc, help_n) == 1)
+            lane_phase(tab, n_sys, ic, out, part, n_virt, n_carry, ctr, ready, susp, cap, refill, budget, true);
     }
     if ((threadIdx.x & 31) == 0) atomicMax(&ctr->t_end, global_ns());
 }
@@ -886,10 +1029,15 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sched(const SysDev* __restrict_
 // Finishes suspend records left by k_sched (normally none: its workers drain them).
 template <int G>
 __global__ void __launch_bounds__(128) k_tail(const SysDev* __restrict__ tab, IcPtrs ic, ObsPtrs out,
-                                              const Susp* __restrict__ susp, const unsigned* __restrict__ ready,
-                                              Counters* __restrict__ ctr, long long cap)
+                                              Susp* __restrict__ susp, unsigned* __restrict__ ready,
+                                              Counters* __restrict__ ctr, long long cap, Part part)
 {
-    tail_phase<G>(tab, ic, out, susp, ready, ctr, cap, false, 0ull);
+    long long n_tc = 0;
+    if (part.tcarry_in_n) {
+        const unsigned long long c = *part.tcarry_in_n;
+        n_tc = c < (unsigned long long)part.tcarry_cap ? (long long)c : part.tcarry_cap;
+    }
+    tail_phase<G>(tab, ic, out, susp, ready, ctr, cap, false, 0ull, part, n_tc);
     if ((threadIdx.x & 31) == 0) atomicMax(&ctr->t_end, global_ns());
 }
 
@@ -1249,6 +1397,20 @@ struct ia_graph {
     cudaGraphExec_t exec;
 };
 
+struct ia_queue {
+    ia_system* sys;
+    int64_t n;                // trajectories of the batch
+    ia_launch_opts opts;      // launch options fixed at creation
+    void* scratch;            // counters, ready flags, suspend records, two carry buffers
+    size_t bytes;
+    size_t carry_off;         // byte offset of the carry buffers
+    long long carry_cap;      // records per lane-mode carry buffer (one per lane of the grid)
+    long long tcarry_cap;     // records per group-mode carry buffer
+    int64_t started;          // queue positions handed to parts so far
+    int64_t parts;            // parts launched since creation or the last reset
+    const void* bound[18];    // the arrays of the batch, fixed by its first part
+};
+
 namespace {
 
 bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
@@ -1437,6 +1599,88 @@ const void* sched_fn(int block, int minb, int g)
     return (const void*)k_sched<128, 1, 6>;
 }
 
+// Launch configuration of the fused kernel for resolved options on the system's device.
+struct SchedCfg {
+    const void* fn;
+    int block, grid, resident, budget, wait_ok, tail_sms, pair, refill;
+};
+
+int sched_config(const ia_system* sys, const Resolved& r, SchedCfg& c)
+{
+    const ia_launch_opts& o = r.o;
+    c.block = o.block == 0 ? 128 : o.block;
+    if (c.block != 64 && c.block != 128 && c.block != 256) return IA_ERR_INVALID_ARG;
+    if (o.regs_variant != 0 && o.regs_variant != 1 && !(o.regs_variant == 3 && c.block == 128))
+        return IA_ERR_INVALID_ARG;
+    if (o.tail_group == 8 && (c.block != 128 || o.regs_variant == 3)) return IA_ERR_INVALID_ARG;
+    const int minb = o.regs_variant == 3 ? 3 : 1;
+    c.fn = sched_fn(c.block, minb, o.tail_group);
+    c.resident = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.resident, c.fn, c.block, 0) != cudaSuccess ||
+        c.resident <= 0)
+        return IA_ERR_CUDA;
+    c.grid = o.grid;
+    if (c.grid == 0) {
+        int nb = c.resident;
+        if (o.blocks_per_sm > 0 && o.blocks_per_sm < nb) nb = o.blocks_per_sm;
+        c.grid = nb * sys->num_sms;
+    }
+    // Waiting for records across blocks needs every block resident: a cooperative launch gives that.
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, sys->device);
+    c.budget = o.slice_budget > 0 ? o.slice_budget : 0;
+    c.wait_ok = (c.budget > 0 && coop && c.grid <= c.resident * sys->num_sms) ? 1 : 0;
+    c.tail_sms = (c.wait_ok && o.tail_sms > 0) ? o.tail_sms : 0;
+    if (c.tail_sms > sys->num_sms / 2) c.tail_sms = sys->num_sms / 2;
+    c.pair = (o.tail_group != 8 && o.tail_pair == 1) ? 1 : 0;
+    c.refill = o.refill;
+    return IA_OK;
+}
+
+// One launch of the fused kernel on `part` (plus, for the last part of a batch, the clean-up tail
+// kernel). The scratch counters the launch needs at zero are cleared by the caller.
+int launch_sched(const ia_system* sys, const SchedCfg& c, const Resolved& r, IcPtrs icp, ObsPtrs op, Part part,
+                 char* scratch, cudaStream_t st)
+{
+    Counters* ctr = reinterpret_cast<Counters*>(scratch);
+    unsigned* ready = reinterpret_cast<unsigned*>(scratch + SCRATCH_HEAD);
+    Susp* susp = reinterpret_cast<Susp*>(scratch + SCRATCH_HEAD + ready_bytes(r.cap));
+    long long cap = r.cap;
+    int refill = c.refill, budget = c.budget, tail_sms = c.tail_sms, wait_ok = c.wait_ok, pair = c.pair;
+    int n_sys = sys->n_sys;
+    const SysDev* tab = sys->d_tab;
+    void* args[] = {(void*)&tab, (void*)&n_sys, (void*)&icp, (void*)&op, (void*)&part, (void*)&ctr, (void*)&ready,
+                    (void*)&susp, (void*)&cap, (void*)&refill, (void*)&budget, (void*)&tail_sms, (void*)&wait_ok,
+                    (void*)&pair};
+    cudaError_t e;
+    if (wait_ok)
+        e = cudaLaunchCooperativeKernel(c.fn, dim3(c.grid), dim3(c.block), args, 0, st);
+    else
+        e = cudaLaunchKernel(c.fn, dim3(c.grid), dim3(c.block), args, 0, st);
+    if (e != cudaSuccess) return IA_ERR_CUDA;
+    if (budget > 0 && part.last && !part.lane_only) {
+        // records the fused kernel could not finish (normally none)
+        const int tgrid = r.o.tail_blocks_per_sm * sys->num_sms;
+        if (r.o.tail_group == 8)
+            k_tail<8><<<tgrid, 128, 0, st>>>(tab, icp, op, susp, ready, ctr, cap, part);
+        else
+            k_tail<6><<<tgrid, 128, 0, st>>>(tab, icp, op, susp, ready, ctr, cap, part);
+        if (cudaGetLastError() != cudaSuccess) return IA_ERR_CUDA;
+    }
+    return IA_OK;
+}
+
+// The whole batch as one part (ia_launch, ia_graph_create, ia_launch_static).
+Part single_part(long long n)
+{
+    Part p;
+    std::memset(&p, 0, sizeof(p));
+    p.first = 0;
+    p.count = n;
+    p.last = 1;
+    return p;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1574,6 +1818,9 @@ int ia_launch(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* 
         return cudaGetLastError() == cudaSuccess ? IA_OK : IA_ERR_CUDA;
     }
 
+    SchedCfg cfg;
+    rc = sched_config(sys, r, cfg);
+    if (rc != IA_OK) return rc;
     // scratch: caller's, else the system's own (grown here if needed: not inside a stream capture)
     char* scratch = nullptr;
     if (o.scratch) {
@@ -1585,59 +1832,162 @@ int ia_launch(ia_system* sys, const ia_ic_soa* ic, int64_t n, const ia_obs_soa* 
         if (rc != IA_OK) return rc;
         scratch = static_cast<char*>(sys->d_scratch);
     }
+    if (cudaMemsetAsync(scratch, 0, SCRATCH_HEAD + ready_bytes(r.cap), st) != cudaSuccess) return IA_ERR_CUDA;
+    return launch_sched(sys, cfg, r, icp, op, single_part((long long)n), scratch, st);
+}
 
-    const int block = o.block == 0 ? 128 : o.block;
-    if (block != 64 && block != 128 && block != 256) return IA_ERR_INVALID_ARG;
-    if (o.regs_variant != 0 && o.regs_variant != 1 && !(o.regs_variant == 3 && block == 128))
-        return IA_ERR_INVALID_ARG;
-    if (o.tail_group == 8 && (block != 128 || o.regs_variant == 3)) return IA_ERR_INVALID_ARG;
-    const int minb = o.regs_variant == 3 ? 3 : 1;
-    const void* fn = sched_fn(block, minb, o.tail_group);
-    int resident = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fn, block, 0) != cudaSuccess || resident <= 0)
-        return IA_ERR_CUDA;
-    int grid = o.grid;
-    if (grid == 0) {
-        int nb = resident;
-        if (o.blocks_per_sm > 0 && o.blocks_per_sm < nb) nb = o.blocks_per_sm;
-        grid = nb * sys->num_sms;
-    }
-    // Waiting for records across blocks needs every block resident: a cooperative launch gives that.
+// ---------------------------------------------------------------------------------------------
+// A batch integrated over several launches (ia_queue)
+
+int ia_queue_create(ia_system* sys, int64_t n, const ia_launch_opts* opts, ia_queue** q)
+{
+    if (!sys || !q || n < 1) return IA_ERR_INVALID_ARG;
+    ia_launch_opts o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (o.kernel == IA_KERNEL_PLAIN) o.kernel = IA_KERNEL_PERSISTENT;
+    if (o.scratch != nullptr || o.scratch_bytes != 0 || o.tail_pair == 1) return IA_ERR_INVALID_ARG;
+    Resolved r;
+    int rc = resolve(n, &o, r);
+    if (rc != IA_OK) return rc;
+    SchedCfg cfg;
+    rc = sched_config(sys, r, cfg);
+    if (rc != IA_OK) return rc;
+    // every block must be resident (the parts end on a grid-wide condition)
+    if (cfg.grid > cfg.resident * sys->num_sms) return IA_ERR_INVALID_ARG;
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, sys->device);
-    const int budget = o.slice_budget > 0 ? o.slice_budget : 0;
-    int wait_ok = (budget > 0 && coop && grid <= resident * sys->num_sms) ? 1 : 0;
-    int tail_sms = (wait_ok && o.tail_sms > 0) ? o.tail_sms : 0;
-    if (tail_sms > sys->num_sms / 2) tail_sms = sys->num_sms / 2;
-
-    Counters* ctr = reinterpret_cast<Counters*>(scratch);
-    unsigned* ready = reinterpret_cast<unsigned*>(scratch + SCRATCH_HEAD);
-    Susp* susp = reinterpret_cast<Susp*>(scratch + SCRATCH_HEAD + ready_bytes(r.cap));
-    if (cudaMemsetAsync(scratch, 0, SCRATCH_HEAD + ready_bytes(r.cap), st) != cudaSuccess) return IA_ERR_CUDA;
-    long long cap = r.cap;
-    long long nn = (long long)n;
-    int refill = o.refill;
-    int n_sys = sys->n_sys;
-    const SysDev* tab = sys->d_tab;
-    int pair = (o.tail_group != 8 && o.tail_pair == 1) ? 1 : 0;
-    void* args[] = {(void*)&tab, (void*)&n_sys, (void*)&icp, (void*)&op, (void*)&nn, (void*)&ctr, (void*)&ready,
-                    (void*)&susp, (void*)&cap, (void*)&refill, (void*)&budget, (void*)&tail_sms, (void*)&wait_ok,
-                    (void*)&pair};
-    cudaError_t e;
-    if (wait_ok)
-        e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, st);
-    else
-        e = cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, st);
-    if (e != cudaSuccess) return IA_ERR_CUDA;
-    if (budget > 0) {
-        // records the fused kernel could not finish (normally none)
-        const int tgrid = o.tail_blocks_per_sm * sys->num_sms;
-        if (o.tail_group == 8)
-            k_tail<8><<<tgrid, 128, 0, st>>>(tab, icp, op, susp, ready, ctr, cap);
-        else
-            k_tail<6><<<tgrid, 128, 0, st>>>(tab, icp, op, susp, ready, ctr, cap);
-        if (cudaGetLastError() != cudaSuccess) return IA_ERR_CUDA;
+    if (!coop) return IA_ERR_NO_DEVICE;
+    const long long carry_cap = (long long)cfg.grid * cfg.block;  // one record per lane of the grid
+    // one group-mode record per trajectory the reserved SMs' tail warps can hold
+    const long long tcarry_cap = (long long)(cfg.tail_sms > 0 ? cfg.tail_sms : 1) * TAIL_WARPS * 5;
+    const size_t carry_off = r.bytes;
+    const size_t bytes = carry_off + 2 * (size_t)(carry_cap + tcarry_cap) * sizeof(Susp);
+    ia_queue* Q = new (std::nothrow) ia_queue;
+    if (!Q) return IA_ERR_INVALID_ARG;
+    Q->scratch = nullptr;
+    if (cudaMalloc(&Q->scratch, bytes) != cudaSuccess) {
+        delete Q;
+        return IA_ERR_CUDA;
     }
+    Q->sys = sys;
+    Q->n = n;
+    Q->opts = o;
+    Q->bytes = bytes;
+    Q->carry_off = carry_off;
+    Q->carry_cap = carry_cap;
+    Q->tcarry_cap = tcarry_cap;
+    Q->started = 0;
+    Q->parts = 0;
+    std::memset(Q->bound, 0, sizeof(Q->bound));
+    *q = Q;
+    return IA_OK;
+}
+
+int ia_queue_launch(ia_queue* q, const ia_ic_soa* ic, const ia_obs_soa* out, int64_t count, void* stream)
+{
+    if (!q || !ic || !out || count < 0) return IA_ERR_INVALID_ARG;
+    ia_system* sys = q->sys;
+    const int64_t n = q->n;
+    if (q->started >= n || count > n - q->started) return IA_ERR_INVALID_ARG;
+    if (!ic->y0 || !ic->phi0 || ic->ld < n) return IA_ERR_INVALID_ARG;
+    if (!out->theta_s || !out->dp || !out->dE_ion || !out->t_final || !out->t_first_bounce ||
+        !out->t_last_bounce || !out->n_bounce || !out->status || !out->n_steps || !out->n_rej)
+        return IA_ERR_INVALID_ARG;
+    if (out->y_final && out->ld < n) return IA_ERR_INVALID_ARG;
+    if (!aligned8(ic->y0) || !aligned8(ic->phi0) || !aligned8(out->theta_s) || !aligned8(out->dp) ||
+        !aligned8(out->dE_ion) || !aligned8(out->t_final) || !aligned8(out->t_first_bounce) ||
+        !aligned8(out->t_last_bounce) || (out->y_final && !aligned8(out->y_final)) ||
+        (ic->order && !aligned8(ic->order)))
+        return IA_ERR_ALIGNMENT;
+    // the records of running trajectories hold batch indices: every part sees the same arrays
+    const void* ptrs[18] = {ic->y0, ic->phi0, ic->sys_id, ic->order, (const void*)(intptr_t)ic->ld,
+                            out->theta_s, out->dp, out->dE_ion, out->t_final, out->t_first_bounce,
+                            out->t_last_bounce, out->n_bounce, out->status, out->n_steps, out->n_rej,
+                            out->y_final, (const void*)(intptr_t)(out->y_final ? out->ld : 0), nullptr};
+    if (q->parts == 0) {
+        std::memcpy(q->bound, ptrs, sizeof(ptrs));
+    } else if (std::memcmp(q->bound, ptrs, sizeof(ptrs)) != 0) {
+        return IA_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != sys->device) return IA_ERR_INVALID_ARG;
+    Resolved r;
+    int rc = resolve(n, &q->opts, r);
+    if (rc != IA_OK) return rc;
+    SchedCfg cfg;
+    rc = sched_config(sys, r, cfg);
+    if (rc != IA_OK) return rc;
+    if ((long long)cfg.grid * cfg.block > q->carry_cap) return IA_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* scratch = static_cast<char*>(q->scratch);
+    Counters* ctr = reinterpret_cast<Counters*>(scratch);
+    Susp* carry = reinterpret_cast<Susp*>(scratch + q->carry_off);
+    const int in = q->parts & 1, outb = in ^ 1;
+    Susp* tcarry = carry + 2 * (size_t)q->carry_cap;
+    if (q->parts == 0) {
+        if (cudaMemsetAsync(scratch, 0, SCRATCH_HEAD + ready_bytes(r.cap), st) != cudaSuccess) return IA_ERR_CUDA;
+    } else {
+        if (cudaMemsetAsync(scratch, 0, PER_LAUNCH_BYTES, st) != cudaSuccess ||
+            cudaMemsetAsync(&ctr->carry_n[outb], 0, sizeof(unsigned long long), st) != cudaSuccess ||
+            cudaMemsetAsync(&ctr->tcarry_n[outb], 0, sizeof(unsigned long long), st) != cudaSuccess)
+            return IA_ERR_CUDA;
+    }
+    Part part;
+    part.first = (long long)q->started;
+    part.count = (long long)count;
+    part.carry_in = carry + (size_t)in * (size_t)q->carry_cap;
+    part.carry_in_n = q->parts == 0 ? nullptr : &ctr->carry_n[in];
+    part.last = q->started + count == n ? 1 : 0;
+    part.carry_out = part.last ? nullptr : carry + (size_t)outb * (size_t)q->carry_cap;
+    part.carry_out_n = part.last ? nullptr : &ctr->carry_n[outb];
+    part.carry_cap = q->carry_cap;
+    part.tcarry_in = tcarry + (size_t)in * (size_t)q->tcarry_cap;
+    part.tcarry_in_n = q->parts == 0 ? nullptr : &ctr->tcarry_n[in];
+    part.tcarry_out = part.last ? nullptr : tcarry + (size_t)outb * (size_t)q->tcarry_cap;
+    part.tcarry_out_n = part.last ? nullptr : &ctr->tcarry_n[outb];
+    part.tcarry_cap = q->tcarry_cap;
+    part.lane_only = 0;
+    IcPtrs icp{ic->y0, ic->phi0, ic->sys_id, reinterpret_cast<const long long*>(ic->order), (long long)ic->ld};
+    ObsPtrs op{out->theta_s, out->dp, out->dE_ion, out->t_final, out->t_first_bounce, out->t_last_bounce,
+               out->n_bounce, out->status, out->n_steps, out->n_rej, out->y_final,
+               (long long)(out->y_final ? out->ld : 0)};
+    rc = launch_sched(sys, cfg, r, icp, op, part, scratch, st);
+    if (rc != IA_OK) return rc;
+    q->started += count;
+    q->parts += 1;
+    return IA_OK;
+}
+
+int ia_queue_reset(ia_queue* q)
+{
+    if (!q) return IA_ERR_INVALID_ARG;
+    q->started = 0;
+    q->parts = 0;
+    std::memset(q->bound, 0, sizeof(q->bound));
+    return IA_OK;
+}
+
+int ia_queue_state(const ia_queue* q, int64_t* started, int64_t* parts, int64_t* n)
+{
+    if (!q) return IA_ERR_INVALID_ARG;
+    if (started) *started = q->started;
+    if (parts) *parts = q->parts;
+    if (n) *n = q->n;
+    return IA_OK;
+}
+
+int ia_queue_phases(const ia_queue* q, double* lane_ms, double* total_ms, int64_t* errors)
+{
+    if (!q || q->parts == 0) return IA_ERR_INVALID_ARG;
+    return ia_launch_phases(q->sys, q->scratch, lane_ms, total_ms, errors);
+}
+
+int ia_queue_destroy(ia_queue* q)
+{
+    if (!q) return IA_OK;
+    cudaFree(q->scratch);
+    delete q;
     return IA_OK;
 }
 
@@ -1818,7 +2168,9 @@ int ia_autotune(ia_system* sys, const ia_ic_soa* ic, int64_t n, int32_t attempt_
         int refill = cd.refill, budget = attempt_cap, tail_sms = 0, wait_ok = 0, pair = 0, n_sys = sys->n_sys;
         long long capv = cap;
         const SysDev* tab = sys->d_tab;
-        void* args[] = {(void*)&tab, (void*)&n_sys, (void*)&icp, (void*)&op, (void*)&nn_, (void*)&ctr,
+        Part part = single_part(nn_);
+        part.lane_only = 1;  // every trajectory stops at the cap (its suspend record is never resumed)
+        void* args[] = {(void*)&tab, (void*)&n_sys, (void*)&icp, (void*)&op, (void*)&part, (void*)&ctr,
                         (void*)&ready, (void*)&susp, (void*)&capv, (void*)&refill, (void*)&budget,
                         (void*)&tail_sms, (void*)&wait_ok, (void*)&pair};
         if (cudaMemsetAsync(scr, 0, SCRATCH_HEAD + ready_bytes(cap), st) != cudaSuccess) rc = IA_ERR_CUDA;
@@ -2171,16 +2523,50 @@ static __device__ __align__(256) unsigned char g_ia_static_scratch[IA_STATIC_SCR
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 void* g_static_addr[kMaxDevices] = {};
+unsigned long long g_static_ctx[kMaxDevices] = {};
 
-// Device address of g_ia_static_scratch on the current device (looked up once per device).
+// Identity of the calling thread's current CUDA context (unique for the life of the process), or 0
+// when it cannot be told. A device reset destroys the context that loaded the library's device code;
+// the array then lives at a new address in the next context, so the cached address is keyed on this.
+// The driver functions are reached through the runtime's entry-point query (no link to the driver).
+unsigned long long current_context_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of g_ia_static_scratch on the current device: looked up once per device and context
+// (again after a device reset; every call when the context cannot be identified).
 int static_scratch_address(int dev, void** out)
 {
     if (dev < 0 || dev >= kMaxDevices) return IA_ERR_NO_DEVICE;
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_static_addr[dev] || ctx == 0 || g_static_ctx[dev] != ctx) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_ia_static_scratch) != cudaSuccess || !p) return IA_ERR_CUDA;
         g_static_addr[dev] = p;
+        g_static_ctx[dev] = ctx;
     }
     *out = g_static_addr[dev];
     return IA_OK;
@@ -2208,4 +2594,21 @@ extern "C" int ia_launch_static(ia_system* sys, const ia_ic_soa* ic, int64_t n, 
     o.scratch = p;
     o.scratch_bytes = (int64_t)IA_STATIC_SCRATCH_BYTES;
     return ia_launch(sys, ic, n, out, &o, stream);
+}
+
+extern "C" int ia_static_phases(ia_system* sys, double* lane_ms, double* total_ms, int64_t* errors)
+{
+    if (!sys || !lane_ms || !total_ms) return IA_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return IA_ERR_NO_DEVICE;
+    if (dev != sys->device) return IA_ERR_INVALID_ARG;
+    // the counters sit at the start of the array; read them by symbol (no device address needed)
+    Counters c;
+    if (cudaMemcpyFromSymbol(&c, g_ia_static_scratch, sizeof(Counters), 0, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return IA_ERR_CUDA;
+    if (c.t_start == 0 || c.t_end < c.t_start) return IA_ERR_INVALID_ARG;
+    *lane_ms = c.t_lane_end >= c.t_start ? 1e-6 * (double)(c.t_lane_end - c.t_start) : 0.0;
+    *total_ms = 1e-6 * (double)(c.t_end - c.t_start);
+    if (errors) *errors = (int64_t)c.errors;
+    return IA_OK;
 }

@@ -814,6 +814,34 @@ __device__ __forceinline__ void lane_suspend(const Lane& L, long long idx, int s
     rec->flags = (L.s.nofailed ? 1 : 0) | (L.s.retry ? 2 : 0);
 }
 
+// Load a saved trajectory back into a lane (the inverse of lane_suspend): the lane continues with the
+// same state and controller scalars, so it produces the bits it would have produced without the stop.
+// The record was written by an earlier kernel launch, so plain loads see it.
+__device__ __forceinline__ void lane_resume(const Susp* __restrict__ rec, Lane& L, long long& idx, int& sid)
+{
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        L.xi[j] = rec->x[j]; L.xa[j] = rec->x[3 + j];
+        L.vi[j] = rec->v[j]; L.va[j] = rec->v[3 + j];
+        L.a1i[j] = rec->a1[j]; L.a1a[j] = rec->a1[3 + j];
+    }
+    L.s.t = rec->t;
+    L.s.h = rec->h;
+    L.s.hmin = hmin_at(L.s.t);  // the value attempt_begin set for the step in progress
+    L.s.phi0 = rec->phi0;
+    L.s.rdot_prev = rec->rdot_prev;
+    L.s.t_first = rec->t_first;
+    L.s.t_last = rec->t_last;
+    L.s.n_acc = rec->n_acc;
+    L.s.n_rej = rec->n_rej;
+    L.s.n_bounce = rec->n_bounce;
+    const int flags = rec->flags;
+    L.s.nofailed = (flags & 1) != 0;
+    L.s.retry = (flags & 2) != 0;
+    idx = rec->idx;
+    sid = rec->sid;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Group mode: lanes base .. base + G - 1 of a warp hold one trajectory; lane comp c < 6 holds
 // component c of [x_ion, x_atom] (lanes with c >= 6 compute on a copy of component 5 and are never

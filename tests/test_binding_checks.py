@@ -81,9 +81,16 @@ def test_conforming_tensors_reach_the_library(rec):
     Bd.ia_sample_ics(smp, 5, big[:, :N], p)
     Bd.ia_philox4x64(1, 2, 3, 0, torch.zeros((N, 4), dtype=torch.int64))
     Bd.ia_rcp_check(p, torch.zeros(N, dtype=torch.float64))
+    Q = Bd.Queue(1, N, slice_budget=300)
+    Q.launch(y, p, s, out, 5, order=order)
+    Q.launch(y, p, s, out, N - 5, order=order)
+    Q.state()
+    Q.reset()
     assert rec.calls.count("ia_launch") == 5 and rec.calls.count("ia_launch_adjoint") == 3
+    assert rec.calls.count("ia_queue_launch") == 2
     for name in ("ia_launch_static", "ia_reduce_stats", "ia_graph_create", "ia_autotune", "ia_launch_tangent",
-                 "ia_sample_ics", "ia_philox4x64", "ia_rcp_check"):
+                 "ia_sample_ics", "ia_philox4x64", "ia_rcp_check", "ia_queue_create", "ia_queue_state",
+                 "ia_queue_reset"):
         assert name in rec.calls, name
 
 
@@ -126,6 +133,11 @@ def test_wrong_tensors_are_refused_before_the_library(rec):
     refused(Bd.ia_philox4x64, 1, 2, 3, 0, torch.zeros((N, 3), dtype=torch.int64))
     refused(Bd.ia_sample_ics, Bd.ia_sampler(), 0, y[:, :5], p)
     refused(Bd.ia_launch, 1, y, p, s, out, scratch=torch.zeros((8, 8), dtype=torch.float64).t())
+    Q = Bd.Queue(1, N)
+    rec.calls.clear()
+    refused(Q.launch, y[:, :N - 1], p[:N - 1].contiguous(), s[:N - 1].contiguous(), out, 3)  # not the queue's n
+    refused(Q.launch, y, p, s, Bd.alloc_obs(N - 1, device="cpu"), 3)
+    refused(Q.launch, y.float(), p, s, out, 3)
     assert rec.calls == []
 
 

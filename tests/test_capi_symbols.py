@@ -63,6 +63,13 @@ def test_invalid_arguments_rejected_without_touching_gpu():
     assert L.ia_system_create(None, 1, None) == -1
     assert L.ia_system_count(None) == -1
     assert L.ia_system_destroy(None) == 0
+    assert L.ia_queue_create(None, 10, None, None) == -1
+    assert L.ia_queue_launch(None, None, None, 0, None) == -1
+    assert L.ia_queue_reset(None) == -1
+    assert L.ia_queue_state(None, None, None, None) == -1
+    assert L.ia_queue_phases(None, None, None, None) == -1
+    assert L.ia_queue_destroy(None) == 0
+    assert L.ia_static_phases(None, None, None, None) == -1
     # scratch sizing is pure host arithmetic
     head = 1024
     assert Bd.ia_scratch_bytes(0) == head

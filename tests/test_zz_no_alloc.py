@@ -42,6 +42,7 @@ def test_static_launch_matches_launch_twice_in_a_row(cuda):
             out = Bd.alloc_obs(n, y_final=True)
             Bd.ia_launch_static(S.handle, yd, pd, sd, out, **kw)
             torch.cuda.synchronize()
+            assert Bd.ia_static_phases(S.handle)[2] == 0, f"call {call}: a bounded wait ran out"
             got = _results(out)
             # same kernels and arithmetic: identical bits (tighter than the parity tolerance)
             for k in ref:
