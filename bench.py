@@ -48,14 +48,14 @@ FLOPS_PER_ATTEMPT = 884.0
 DRAM_BYTES_PER_TRAJECTORY = 148.0
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=1)
-    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--stride", type=int, default=1, help="grid stride of the per-step batch (1: the whole sweep)")
-    p.add_argument("--warmup-stride", type=int, default=64)
+    p.add_argument("--stride", type=int, default=1, help="grid stride of the batch (1: the whole sweep)")
+    p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -67,16 +67,18 @@ def parse():
     p.add_argument("--tail-group", type=int, default=0)
     p.add_argument("--tail-blocks-per-sm", type=int, default=0)
     p.add_argument("--tail-sms", type=int, default=0)
-    p.add_argument("--tail-pair", type=int, default=0, help="1: paired tail warps on the reserved SMs; 0: off")
-    p.add_argument("--diff-sample", type=int, default=4096,
+    p.add_argument("--diff-sample", type=int, default=16384,
                    help="trajectories of the differentiation workload timed through the tangent and adjoint "
                         "kernels (0: skip)")
+    p.add_argument("--diff-cap", type=int, default=1 << 16,
+                   help="attempted steps after which each trajectory of that side measurement stops (0: none)")
     p.add_argument("--workload", default="sweep",
-                   choices=["sweep", "thermal", "mixed-graph", "ftle", "sampler", "energy-scan", "thermal-sweep",
-                            "lifetimes"],
+                   choices=["sweep", "thermal", "mixed-graph", "ftle", "diff", "sampler", "energy-scan",
+                            "thermal-sweep", "lifetimes"],
                    help="sweep: the species x energy step (the bench line); thermal: the Monte Carlo bath; "
                         "mixed-graph: the 250-cell parameter sweep replayed as one CUDA graph with statistics; "
-                        "ftle: the tangent kernel on the FTLE grid; sampler: initial conditions drawn on the "
+                        "ftle: the tangent kernel on the FTLE grid; diff: tangent and adjoint kernels on the "
+                        "differentiation workload (uncapped); sampler: initial conditions drawn on the "
                         "device; energy-scan: the collision-energy scan with device-drawn initial conditions, "
                         "per-cell statistics and the threshold fit; thermal-sweep: the species x T x D_e "
                         "thermal runs with the paper's sphere sampler on the device; lifetimes: complex "
@@ -89,7 +91,7 @@ def parse():
                    help="run the persistent and plain kernels once on a small batch (for ncu) and exit")
     p.add_argument("--profile-grid", type=int, default=64,
                    help="(theta, phi) grid points per direction of the profile case")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 def profile_case(n_grid: int = 64):
@@ -115,18 +117,23 @@ def profile_case(n_grid: int = 64):
                       "attempted_steps": n}))
 
 
-def diff_bench(n: int, flush):
+def diff_bench(n: int, flush, cap: int = 0):
     """Tangent (4 seeds + FTLE) and adjoint (4 objectives, projected on the same seeds) launches on the
     first n trajectories of the differentiation workload (Yb+-Rb head-on, 1.5 uK, (theta, phi) uniform
     on the octant, seed 5), each timed with CUDA events after a warm-up launch on 64 of them, next to
-    the persistent primal launch on the same trajectories."""
+    the persistent primal launch on the same trajectories. cap > 0 stops every trajectory after that
+    many attempted steps (the same in all three launches), so that the measurement is bounded by
+    throughput rather than by the few longest complexes."""
     import torch
     from paper_2509_15117_gb300 import binding as Bd
     sysd, y0, phi0, seeds, dq = I.c5_workload(n)
     dy0 = np.concatenate([seeds, np.zeros((n, 1, 12))], axis=1)
     stream = torch.cuda.current_stream()
     res = {}
-    with Bd.System([sysd.as_dict()]) as S:
+    desc = sysd.as_dict()
+    if cap > 0:
+        desc["max_attempts"] = int(cap)
+    with Bd.System([desc]) as S:
         def run(kind, m):
             y, p, _ = Bd.to_device_soa(y0[:m], phi0[:m], None)
             dyd = torch.from_numpy(np.ascontiguousarray(np.transpose(dy0[:m], (1, 2, 0)))).cuda()
@@ -155,13 +162,16 @@ def diff_bench(n: int, flush):
             ms, att = run(kind, n)
             res[kind] = (ms, att)
     wl = ("Yb+-Rb head-on, E = 1.5 uK, D_e = 1 K, q = 0.1, t_max = 1 ms, (theta, phi) uniform on the "
-          f"octant (seed 5), first {n} trajectories")
+          f"octant (seed 5), first {n} trajectories" + (f", each stopped after at most {cap} attempted steps"
+                                                        if cap > 0 else ""))
     base = {"unit": UNIT, "trajectories": n, "workload": wl,
             "attempted_steps_per_trajectory": res["primal"][1] / n,
             "primal_persistent_ms_same_sample": res["primal"][0]}
     tan = dict(base, value=n / (res["tangent"][0] / 1e3), ms=res["tangent"][0], directions=4, ftle=True,
+               attempted_steps_per_s=res["tangent"][1] / (res["tangent"][0] / 1e3),
                cost_vs_primal=res["tangent"][0] / res["primal"][0])
     adj = dict(base, value=n / (res["adjoint"][0] / 1e3), ms=res["adjoint"][0], objectives=4, seeds=4,
+               attempted_steps_per_s=res["adjoint"][1] / (res["adjoint"][0] / 1e3),
                checkpoint_every=10000, cost_vs_primal=res["adjoint"][0] / res["primal"][0])
     return tan, adj
 
@@ -181,6 +191,13 @@ def secondary(args):
     if args.workload == "lifetimes":
         lifetimes(args)
         return
+    if args.workload == "diff":
+        n = int(args.scale) if args.scale > 0 else 1 << 20
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        tan, adj = diff_bench(n, flush, 0)
+        print(json.dumps({"metric": METRIC, "workload": "diff", "tangent": tan, "adjoint": adj,
+                          "gpu_launches": 6, "dtype": "f64", "data": "synthetic"}), flush=True)
+        return
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     if args.workload == "sampler":
@@ -190,17 +207,17 @@ def secondary(args):
         return
     extra = {}
     if args.workload == "thermal":
-        n_per = int(args.scale * 1e7) if args.scale > 0 else 1 << 20
+        n_per = int(args.scale * 1e7) if args.scale > 0 else 10_000_000
         systems, y0, phi0, sid = I.c3_workload(n_per)
         desc = (f"Yb+-Rb Monte Carlo bath, disk sampler b_max 2000 a0, T = 10 uK, 100 uK, 1 mK, {n_per} "
                 f"trajectories each (seeds 3001-3003), random rf phase, ion at 10 uK with micromotion")
     elif args.workload == "mixed-graph":
-        scale = args.scale if args.scale > 0 else 0.25
+        scale = args.scale if args.scale > 0 else 1.0
         systems, y0, phi0, sid = I.c4_workload(scale=scale)
         desc = (f"250 cells D_e x q x a x species, 4096..262144 trajectories per cell x {scale}, head-on at "
                 f"1.5 uK, random rf phase; launch + per-cell statistics replayed as one CUDA graph")
     else:
-        sysd, y0, phi0, seeds = I.c5_ftle_grid(int(args.scale) if args.scale > 0 else 256)
+        sysd, y0, phi0, seeds = I.c5_ftle_grid(int(args.scale) if args.scale > 0 else 2048)
         systems, sid = [sysd], np.zeros(len(phi0), dtype=np.int32)
         desc = (f"tangent kernel (1 direction + FTLE) on the {int(round(len(phi0) ** 0.5))}^2 cell-centred "
                 f"octant grid, Yb+-Rb head-on 1.5 uK, rf phase 0")
@@ -725,13 +742,58 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def step_inputs(step, stride, rank, world):
-    """Inputs of one step, in queue order (longest expected first)."""
+def sweep_in_queue_order(stride: int, offset: int):
+    """The species x energy sweep (every stride-th grid point from offset) laid out in queue order
+    (systems by expected cost, costliest first; see schedule.py), so that each part of the queue is a
+    contiguous range of the arrays. Returns the systems, the pinned host arrays (SoA state (12, n),
+    phases, system ids) and the permutation from queue position to grid order."""
+    import torch
     from paper_2509_15117_gb300 import schedule as Sch
-    systems, y0, phi0, sid = batch(step, stride, rank, world)
+    systems, y0, phi0, sid = I.c2_workload(n_grid=GRID, stride=stride, offset=offset)
     speeds = [I.speed_for_energy(I.kelvin(E), s.m_atom) for (sp, E, s) in I.c2_systems()]
     order = Sch.order_by_cost(sid, Sch.system_cost(systems, speeds))
-    return systems, y0, phi0, sid, order
+    n = len(phi0)
+    hy = torch.empty((12, n), dtype=torch.float64).pin_memory()
+    hyn = hy.numpy()
+    for c in range(12):
+        np.take(y0[:, c], order, out=hyn[c])
+    del y0
+    hp = torch.from_numpy(phi0[order]).pin_memory()
+    hs = torch.from_numpy(sid[order]).pin_memory()
+    return systems, hy, hp, hs, order
+
+
+def part_bounds(n: int, parts: int) -> np.ndarray:
+    """Queue positions where each of `parts` equal parts of an n-trajectory batch starts (and n)."""
+    return np.linspace(0, n, parts + 1).round().astype(np.int64)
+
+
+def lane_options(args, handle, y, p, d, n_sample: int, attempt_cap: int):
+    """Launch options of the queue: the autotuner's pick of block, register variant and refill on a
+    random sample of the batch (unless --no-autotune or an explicit --block); the reserved tail SMs
+    (a reserved SM keeps up to 4 tail warps, one per sub-partition) sized so that the tail has 128
+    warps whatever the block size."""
+    import torch
+    from paper_2509_15117_gb300 import binding as Bd
+    kw = {"block": args.block, "refill": args.refill, "blocks_per_sm": args.blocks_per_sm,
+          "regs_variant": args.regs_variant, "slice_budget": args.slice_budget, "tail_group": args.tail_group,
+          "tail_blocks_per_sm": args.tail_blocks_per_sm, "tail_sms": args.tail_sms}
+    tune = None
+    if not args.no_autotune and args.block == 0:
+        n = int(p.shape[0])
+        idx = torch.from_numpy(np.sort(np.random.default_rng(99).choice(n, min(n_sample, n), replace=False))).cuda()
+        t0 = time.perf_counter()
+        pick, ms = Bd.ia_autotune(handle, y[:, idx].contiguous(), p[idx].contiguous(), d[idx].contiguous(),
+                                  attempt_cap=attempt_cap)
+        tune = {"pick": pick, "best_ms": ms, "seconds": time.perf_counter() - t0,
+                "sample": f"{int(idx.numel())} trajectories drawn at random (seed 99) from the batch, every "
+                          f"one stopped after {attempt_cap} attempted steps (lane phase only); 9 candidates "
+                          f"(block 64/128/256, register cap 1 or 3 blocks/SM, refill 1/4/16)"}
+        kw.update(pick)
+    block = kw["block"] or 128
+    if args.tail_sms == 0:
+        kw["tail_sms"] = 128 // min(4, block // 32)
+    return kw, tune
 
 
 def main():
@@ -762,119 +824,145 @@ def main():
         torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
-    kw = {"block": args.block, "refill": args.refill, "blocks_per_sm": args.blocks_per_sm,
-          "regs_variant": args.regs_variant, "slice_budget": args.slice_budget, "tail_group": args.tail_group,
-          "tail_blocks_per_sm": args.tail_blocks_per_sm, "tail_sms": args.tail_sms, "tail_pair": args.tail_pair}
-
-    # every step's inputs in pinned host memory and its device buffers (generation outside the timing)
-    steps = []
-    for s in range(args.steps):
-        systems, y0, phi0, sid, order = step_inputs(s, args.stride, rank, world)
-        n = len(phi0)
-        h = {"y": torch.from_numpy(np.ascontiguousarray(y0.T)).pin_memory(),
-             "p": torch.from_numpy(phi0).pin_memory(), "s": torch.from_numpy(sid).pin_memory(),
-             "o": torch.from_numpy(order).pin_memory()}
-        dv = {k: torch.empty(v.shape, dtype=v.dtype, device="cuda") for k, v in h.items()}
-        out = Bd.alloc_obs(n)
-        hout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
-        steps.append({"n": n, "h": h, "d": dv, "out": out, "hout": hout, "order": order})
+    K = args.steps
+    # The batch: the whole sweep (or with --stride S every S-th grid point, a different offset per rank)
+    # in queue order, pinned on the host; the device holds the whole batch, and the K timed steps are
+    # the K parts of one queue over it, so together they integrate every trajectory once.
+    systems, hy, hp, hs, order = sweep_in_queue_order(args.stride, step_offset(0, args.stride, rank, world))
+    n = int(hp.shape[0])
     descs = [s.as_dict() for s in systems]
     sysh = Bd.System(descs)
-    n_max = max(st["n"] for st in steps)
-    Bd.ia_reserve(sysh.handle, n_max, kernel=Bd.IA_KERNEL_PERSISTENT, slice_budget=args.slice_budget)
+    dy = torch.empty_like(hy, device="cuda")
+    dp_ = torch.empty_like(hp, device="cuda")
+    ds = torch.empty_like(hs, device="cuda")
+    out = Bd.alloc_obs(n)
+    hout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
 
-    # warm-up launches of the same kernel on small batches of the workload's short trajectories (the
-    # 1 mK systems of a sparse grid), so that they take seconds, not a long complex's latency
-    for w in range(args.warmup):
-        systems_w, y0, phi0, sid, order = step_inputs(1000 + w, args.warmup_stride, rank, world)
-        keep = np.nonzero(sid % len(I.C2_ENERGIES_K) == len(I.C2_ENERGIES_K) - 1)[0]
-        y, p, d = Bd.to_device_soa(y0[keep], phi0[keep], sid[keep])
-        o = Bd.alloc_obs(len(keep))
-        Bd.ia_launch(sysh.handle, y, p, d, o, **kw)
-    torch.cuda.synchronize()
+    # lane-phase options from the autotuner (inputs copied once for it, overwritten by the timed steps)
+    dy.copy_(hy)
+    dp_.copy_(hp)
+    ds.copy_(hs)
+    kw, tune = lane_options(args, sysh.handle, dy, dp_, ds, 131072, 1024)
+
+    # warm-up: W parts of a queue over the short trajectories of the workload (the 1 mK systems of
+    # every 4th grid point), the same kernel and part logic as the timed steps
+    e_last = len(I.C2_ENERGIES_K) - 1
+    sw, wy, wp, ws, _ = sweep_in_queue_order(4, 0)
+    keep = torch.from_numpy(np.nonzero(ws.numpy() % len(I.C2_ENERGIES_K) == e_last)[0])
+    wy, wp, ws = wy[:, keep].cuda(), wp[keep].cuda(), ws[keep].cuda()
+    nw = int(wp.shape[0])
+    wout = Bd.alloc_obs(nw)
+    with Bd.Queue(sysh.handle, nw, **kw) as QW:
+        wb = part_bounds(nw, max(args.warmup, 1))
+        for k in range(max(args.warmup, 1)):
+            QW.launch(wy, wp, ws, wout, int(wb[k + 1] - wb[k]))
+        torch.cuda.synchronize()
+    del wy, wp, ws, wout
 
     peak_flops = Bd.ia_fp64_peak(4, 20000)
 
-    # timed steps: host -> device copy of the step's inputs, L2 flush, the launch (device-timed for
-    # `value`), device -> host copy of the observables; the whole is the end-to-end time
+    Q = Bd.Queue(sysh.handle, n, **kw)
+    bounds = part_bounds(n, K)
+    fields = list(out.keys())
+    # timed steps: host -> device copy of the part's inputs, L2 flush, the part's launch (device-timed
+    # for `value`), device -> host copy of the part's observables (the last step copies every
+    # observable, since trajectories carried between parts end in later parts); the whole is `e2e`
     clocks = ClockSampler(local)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    phases = []
     barrier()
     clocks.start()
     t0 = time.perf_counter()
-    for s, st in enumerate(steps):
-        ev[s][0].record(stream)
-        for k in st["h"]:
-            st["d"][k].copy_(st["h"][k], non_blocking=True)
+    h2d = d2h = 0
+    for k in range(K):
+        a, b = int(bounds[k]), int(bounds[k + 1])
+        ev[k][0].record(stream)
+        for c in range(12):
+            dy[c, a:b].copy_(hy[c, a:b], non_blocking=True)
+        dp_[a:b].copy_(hp[a:b], non_blocking=True)
+        ds[a:b].copy_(hs[a:b], non_blocking=True)
+        h2d += (b - a) * (12 * 8 + 8 + 4)
         flush.zero_()
-        ev[s][1].record(stream)
-        Bd.ia_launch(sysh.handle, st["d"]["y"], st["d"]["p"], st["d"]["s"], st["out"], order=st["d"]["o"], **kw)
-        ev[s][2].record(stream)
-        for k in st["out"]:
-            st["hout"][k].copy_(st["out"][k], non_blocking=True)
-        ev[s][3].record(stream)
+        ev[k][1].record(stream)
+        Q.launch(dy, dp_, ds, out, b - a)
+        ev[k][2].record(stream)
+        lo, hi = (a, b) if k < K - 1 else (0, n)
+        for f in fields:
+            hout[f][lo:hi].copy_(out[f][lo:hi], non_blocking=True)
+            d2h += (hi - lo) * out[f].element_size()
+        ev[k][3].record(stream)
     barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
-    lane_ms, dev_ms, wait_errors = Bd.ia_launch_phases(sysh.handle)  # the last step's launch
+    lane_ms, dev_ms, wait_errors = Q.phases()  # the last part
     kern_ms = [e[1].elapsed_time(e[2]) for e in ev]
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     total_ms = float(sum(kern_ms))
-    n_local = sum(st["n"] for st in steps)
-    outs = [st["out"] for st in steps]
-    attempts = sum(int((o["n_steps"].to(torch.int64) + o["n_rej"].to(torch.int64)).sum().item()) for o in outs)
-    per = (outs[0]["n_steps"].to(torch.int64) + outs[0]["n_rej"].to(torch.int64)).cpu().numpy()
-    max_attempts = int(max(int((o["n_steps"] + o["n_rej"]).max().item()) for o in outs))
-    longest = int(np.argmax(per))
-    budget_used = args.slice_budget if args.slice_budget > 0 else 131072
+    g_steps = hout["n_steps"].numpy().astype(np.int64)
+    g_rej = hout["n_rej"].numpy().astype(np.int64)
+    per = g_steps + g_rej
+    attempts = int(per.sum())
+    status = hout["status"].numpy().view(np.uint32)
+    status_counts = {nm: int(np.count_nonzero(status & b)) for nm, b in
+                     (("tmax", Bd.ST_TMAX), ("max_steps", Bd.ST_MAX_STEPS), ("h_underflow", Bd.ST_H_UNDERFLOW),
+                      ("nonfinite", Bd.ST_NONFINITE), ("bad_ic", Bd.ST_BAD_IC), ("exit_outside", Bd.ST_EXIT_OUTSIDE))}
+    status_counts["complex"] = int(np.count_nonzero(status & Bd.ST_COMPLEX))
+    max_attempts = int(per.max())
+    budget_used = kw["slice_budget"] if kw["slice_budget"] > 0 else 131072
     long_counts = {f"over_{b}": int((per > b).sum()) for b in (budget_used, 262144, 1048576)}
     top = np.sort(per)[::-1]
     long_counts["top10_attempts"] = [int(v) for v in top[:10]]
     long_counts["attempts_beyond_budget"] = int(np.maximum(per - budget_used, 0).sum())
-    longest_pos = int(np.nonzero(steps[0]["order"] == longest)[0][0])
-    rhs = 6 * attempts + n_local
+    # what other slice budgets would leave to the group-mode tail (attempts beyond each)
+    long_counts["attempts_beyond"] = {str(b): int(np.maximum(per - b, 0).sum())
+                                      for b in (1 << 16, 1 << 17, 1 << 18, 1 << 19, 1 << 20)}
+    long_counts["longest_queue_position"] = int(np.argmax(per)) / n
+    rhs = 6 * attempts + n
     tmax_ms, emax_ms = total_ms, float(sum(step_ms))
     if dist is not None:
         (tmax_ms, emax_ms), (n_all, rhs_all, att_all) = reduce_over_ranks(
-            dist, "cuda", [total_ms, emax_ms], [float(n_local), float(rhs), float(attempts)])
+            dist, "cuda", [total_ms, emax_ms], [float(n), float(rhs), float(attempts)])
     else:
-        n_all, rhs_all, att_all = float(n_local), float(rhs), float(attempts)
+        n_all, rhs_all, att_all = float(n), float(rhs), float(attempts)
     value = n_all / (tmax_ms / 1e3)
     achieved = FLOPS_PER_ATTEMPT * attempts / (total_ms / 1e3)
-    h2d = sum(v.numel() * v.element_size() for v in steps[0]["h"].values())
-    d2h = sum(v.numel() * v.element_size() for v in steps[0]["hout"].values())
-    e2e = {"value": n_all / (emax_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-           "d2h_bytes_per_step": int(d2h), "ms_per_step": emax_ms / args.steps,
-           "path": "ia_launch with the step's inputs copied from pinned host memory and the observables "
-                   "copied back, inside the timed region"}
+    e2e = {"value": n_all / (emax_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d // K),
+           "d2h_bytes_per_step": int(d2h // K), "ms_per_step": emax_ms / K,
+           "path": "ia_queue_launch per step with the part's inputs copied from pinned host memory before it "
+                   "and its observables copied back after it (the last step copies all n), inside the timed "
+                   "region"}
+    Q.close()
+    del dy, dp_, ds
 
-    # plain kernel against the persistent one on a subsample (about 164k trajectories) of the step's batch
+    # plain kernel against the persistent one on a subsample of the batch (every 256th trajectory in
+    # queue order): the plain kernel's warps each wait for their longest lane
     plain = None
     if not args.no_plain:
-        y, p, d, n = steps[0]["d"]["y"], steps[0]["d"]["p"], steps[0]["d"]["s"], steps[0]["n"]
-        every = max(1, int(round(256 / args.stride ** 2)))
-        sub = torch.arange(0, n, every, device="cuda")
-        ys, ps, ds = y[:, sub].contiguous(), p[sub].contiguous(), d[sub].contiguous()
-        m = int(sub.numel())
+        sub = np.arange(0, n, 256)
+        ys = hy[:, torch.from_numpy(sub)].cuda()
+        ps, ss = hp[torch.from_numpy(sub)].cuda(), hs[torch.from_numpy(sub)].cuda()
+        m = len(sub)
         res = {}
-        for name, kk in (("plain", {"kernel": Bd.IA_KERNEL_PLAIN}), ("persistent", dict(kw))):
-            ob = Bd.alloc_obs(m)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            flush.zero_()
-            e0.record(stream)
-            Bd.ia_launch(sysh.handle, ys, ps, ds, ob, **kk)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            res[name] = e0.elapsed_time(e1)
+        with Bd.System(descs) as SC:
+            for name, kk in (("plain", {"kernel": Bd.IA_KERNEL_PLAIN}), ("persistent", dict(kw))):
+                ob = Bd.alloc_obs(m)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.zero_()
+                e0.record(stream)
+                Bd.ia_launch(SC.handle, ys, ps, ss, ob, **kk)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                res[name] = e0.elapsed_time(e1)
         plain = {"value": m / (res["plain"] / 1e3), "unit": UNIT, "trajectories": m, "ms": res["plain"],
                  "persistent_ms_same_batch": res["persistent"],
                  "persistent_speedup": res["plain"] / res["persistent"],
-                 "batch": f"every {every}th trajectory of the step-0 batch, same inputs for both kernels"}
+                 "batch": "every 256th trajectory of the batch in queue order, same inputs for both kernels (both "
+                          "end with the latency of the sample's longest trajectory)"}
 
     diff = None
     if rank == 0 and args.diff_sample > 0:
-        diff = diff_bench(args.diff_sample, flush)
+        diff = diff_bench(args.diff_sample, flush, args.diff_cap)
 
     sampler = None
     if rank == 0 and args.sampler_sample > 0:
@@ -887,40 +975,41 @@ def main():
     sysh.close()
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": tmax_ms / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": tmax_ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {
-                "workload": f"Yb+ head-on species x energy sweep: Li, Na, K, Rb, Cs x 8 energies 1 uK..1 mK, "
-                            f"D_e = 1 K, q = 0.1, a = 0, Omega = 2 pi 2 MHz, t_max = 1 ms, rtol 1e-10; "
-                            + ("the whole 1024^2 octant grid per step" if args.stride == 1 else
-                               f"1024^2 octant grid, every {args.stride}th point per direction per step"),
-                "trajectories_per_step": int(n_all / args.steps), "rtol": 1e-10, "kernel": "persistent",
+                "workload": "Yb+ head-on species x energy sweep: Li, Na, K, Rb, Cs x 8 energies 1 uK..1 mK, "
+                            "D_e = 1 K, q = 0.1, a = 0, Omega = 2 pi 2 MHz, t_max = 1 ms, rtol 1e-10; "
+                            + ("the whole 1024^2 octant grid" if args.stride == 1 else
+                               f"1024^2 octant grid, every {args.stride}th point per direction")
+                            + f" ({int(n_all / world)} trajectories), integrated once over the {K} steps: step k is "
+                              f"part k of one work queue over the batch in queue order",
+                "trajectories_per_step": int(n_all / K), "rtol": 1e-10, "kernel": "persistent (ia_queue)",
                 "queue_order": "systems by sqrt(m_atom)/speed, descending",
-                "l2": "256 MiB buffer written before each step (inputs < L2)",
-                "block": args.block or 128, "refill": args.refill or 1,
-                "slice_budget": args.slice_budget or 131072, "tail_group": args.tail_group or 6,
-                "tail_sms": args.tail_sms or 32, "tail_pair": args.tail_pair == 1 and (args.tail_group or 6) == 6,
+                "l2": "256 MiB buffer written before each step (each part's inputs also exceed L2)",
+                "launch_options": {k_: v for k_, v in kw.items() if v},
+                "autotune": tune,
             },
             "rhs_evals_per_s": rhs_all / (tmax_ms / 1e3),
             "attempted_steps_per_trajectory": att_all / n_all,
             "max_attempted_steps": max_attempts,
-            "longest_trajectory_queue_position": longest_pos / steps[0]["n"],
-            "long_trajectories_step0": long_counts,
+            "status_counts": status_counts,
+            "long_trajectories": long_counts,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_flops / 1e12,
                          "unit": "TFLOP/s", "frac": achieved / peak_flops,
-                         "traffic": DRAM_BYTES_PER_TRAJECTORY * n_local / args.steps,
+                         "traffic": DRAM_BYTES_PER_TRAJECTORY * n / K,
                          "traffic_note": "bytes per launch, ncu DRAM bytes of the 512x512 profile case scaled by "
                                          "trajectories (traffic grows with them: ICs in, observables out)",
                          "peak_source": "FP64 FMA microbenchmark (ia_fp64_peak) measured in this run",
                          "flops_per_attempted_step": FLOPS_PER_ATTEMPT},
             "plain": plain,
             "e2e": e2e,
-            "gpu_launches": args.steps * (1 if args.slice_budget < 0 else 2),
+            "gpu_launches": K + (1 if (kw["slice_budget"] or 0) >= 0 else 0),
+            "step_kernel_ms": [round(x, 3) for x in kern_ms],
             "phases_last_step": {"lane_phase_ms": lane_ms, "kernel_ms": dev_ms, "wait_errors": wait_errors,
-                                 "note": "device clock: until the last warp left the lane phase (every "
-                                         "trajectory started; long ones handed to group mode) / until the "
-                                         "last warp finished"},
+                                 "note": "device clock: until the last warp left the lane phase / until the "
+                                         "last warp finished (the last part drains every carried trajectory)"},
             "clocks": clk,
             "wall_s": wall,
         }

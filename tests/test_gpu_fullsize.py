@@ -1,7 +1,8 @@
 """Parity at full size: the whole species x energy sweep (41,943,040 trajectories) in the launch
-configuration the benchmark times (persistent kernel, default options, queue order), checked against
-the oracle on a seeded random sample of trajectories and, over all of them, against properties that hold
-at any size (needs a GB300; about three minutes)."""
+configuration the benchmark times (one work queue over the batch in queue order, integrated in as many
+parts as the benchmark's default steps, with the autotuner's launch options), checked against the
+oracle on a seeded random sample of trajectories and, over all of them, against properties that hold at
+any size (needs a GB300; about three minutes)."""
 import math
 
 import numpy as np
@@ -27,18 +28,24 @@ def torch_cuda():
 
 def test_whole_sweep_sampled_parity_and_invariants(torch_cuda):
     torch = torch_cuda
-    systems, y0, phi0, sid, order = bench.step_inputs(0, 1, 0, 1)
-    n = len(phi0)
+    args = bench.parse([])
+    systems, hy, hp, hs, order = bench.sweep_in_queue_order(1, 0)
+    n = int(hp.shape[0])
     assert n == 5 * 8 * 1024 * 1024
     descs = [s.as_dict() for s in systems]
     with Bd.System(descs) as S:
-        yd, pd, sd = Bd.to_device_soa(y0, phi0, sid)
+        yd, pd, sd = hy.cuda(), hp.cuda(), hs.cuda()
+        kw, tune = bench.lane_options(args, S.handle, yd, pd, sd, 32768, 2048)
         out = Bd.alloc_obs(n)
-        Bd.ia_launch(S.handle, yd, pd, sd, out, order=torch.from_numpy(order).cuda())
-        torch.cuda.synchronize()
-        assert Bd.ia_launch_phases(S.handle)[2] == 0, "a bounded wait ran out"
+        bounds = bench.part_bounds(n, args.steps)
+        with Bd.Queue(S.handle, n, **kw) as Q:
+            for k in range(args.steps):
+                Q.launch(yd, pd, sd, out, int(bounds[k + 1] - bounds[k]))
+                torch.cuda.synchronize()
+                assert Q.phases()[2] == 0, f"part {k}: a bounded wait ran out"
         del yd, pd, sd
         g = Bd.to_numpy(out)
+    print("launch options", kw, "autotune", tune)
     # properties of every trajectory
     st = g["status"] & 0xFF
     assert not np.any(st & (Bd.ST_BAD_IC | (1 << 3) | (1 << 2) | (1 << 1))), "BAD_IC, NONFINITE, H_UNDERFLOW or MAX_STEPS"
@@ -51,8 +58,10 @@ def test_whole_sweep_sampled_parity_and_invariants(torch_cuda):
     assert np.all(g["n_steps"] >= 1)
     # per-trajectory parity on a seeded random sample, computed one by one by the oracle
     idx = np.sort(np.random.default_rng(20241).choice(n, N_SAMPLE, replace=False))
-    orc, spread = PY.oracle_with_spread(descs, y0[idx], phi0[idx], sid[idx], nthreads=0)
+    y0 = hy.numpy()[:, idx].T.copy()
+    phi0, sid = hp.numpy()[idx], hs.numpy()[idx]
+    orc, spread = PY.oracle_with_spread(descs, y0, phi0, sid, nthreads=0)
     gs = {k: v[idx] for k, v in g.items()}
-    rep = PY.compare(gs, orc, spread, max_flip=0.05)
+    rep = PY.compare(gs, orc, spread)
     print("full-size sampled parity", rep)
     assert rep["n_single"] > N_SAMPLE // 4
