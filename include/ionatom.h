@@ -125,7 +125,11 @@ typedef struct ia_launch_opts {
                                    partitions advance the same trajectories together (a single long
                                    trajectory steps 1.3x faster, but each SM holds half as many;
                                    bit-identical results); 0 or -1 = off (default) */
-    int32_t reserved;           /* must be 0 */
+    int32_t tail_warps;         /* persistent: warps of each reserved SM's block that work on the tail, 1..8
+                                   and at most block/32; 0 = 4 (one per SM sub-partition: a long
+                                   trajectory's latency in group mode is its FP64 instruction count, so a
+                                   tail warp steps fastest with an FP64 unit to itself; 8 trades latency
+                                   for tail throughput). Further warps of that block leave */
     int64_t suspend_capacity;   /* suspend records; 0 = min(n, max(4096, n/32)). A trajectory that finds
                                    no free record is finished by its lane. */
     void* scratch;              /* persistent: caller's device scratch (256-byte aligned), or NULL to use

@@ -145,7 +145,7 @@ class ia_launch_opts(ctypes.Structure):
                 ("refill", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("regs_variant", ctypes.c_int32), ("slice_budget", ctypes.c_int32),
                 ("tail_group", ctypes.c_int32), ("tail_blocks_per_sm", ctypes.c_int32),
-                ("tail_sms", ctypes.c_int32), ("tail_pair", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tail_sms", ctypes.c_int32), ("tail_pair", ctypes.c_int32), ("tail_warps", ctypes.c_int32),
                 ("suspend_capacity", ctypes.c_int64), ("scratch", ctypes.c_void_p), ("scratch_bytes", ctypes.c_int64)]
 
 
@@ -366,7 +366,7 @@ def to_device_soa(y0, phi0, sys_id=None, device="cuda"):
 def make_opts(kernel: int = IA_KERNEL_PERSISTENT, block: int = 0, grid: int = 0, refill: int = 0,
               blocks_per_sm: int = 0, regs_variant: int = 0, slice_budget: int = 0, tail_group: int = 0,
               tail_blocks_per_sm: int = 0, suspend_capacity: int = 0, scratch=None,
-              tail_sms: int = 0, tail_pair: int = 0) -> ia_launch_opts:
+              tail_sms: int = 0, tail_pair: int = 0, tail_warps: int = 0) -> ia_launch_opts:
     opts = ia_launch_opts()
     opts.kernel = kernel
     opts.block = block
@@ -380,6 +380,7 @@ def make_opts(kernel: int = IA_KERNEL_PERSISTENT, block: int = 0, grid: int = 0,
     opts.suspend_capacity = suspend_capacity
     opts.tail_sms = tail_sms
     opts.tail_pair = tail_pair
+    opts.tail_warps = tail_warps
     if scratch is not None:
         _tensor(scratch, "scratch", scratch.dtype, (None,) * scratch.dim())
         opts.scratch = scratch.data_ptr()

@@ -183,15 +183,15 @@ __device__ __forceinline__ int prim_attempt(const SysDev& P, const TLane& tl, in
     const double vn = vel_new(K, v, a1, a3, a4, a5, a6);
     bool okx, fx, okv, fv;
     float rx, rv;
-    err_check(P.rtol, P.atol_pos, x, xn, err_x(K, a1, a3, a4, a5, a6), okx, fx, rx);
-    err_check(P.rtol, P.atol_vel, v, vn, err_v(K, a1, a3, a4, a5, a6, a7), okv, fv, rv);
+    double aex, scx, aev, scv;
+    err_check(P.rtol, P.atol_pos, x, xn, err_x(K, a1, a3, a4, a5, a6), okx, fx, rx, aex, scx);
+    err_check(P.rtol, P.atol_vel, v, vn, err_v(K, a1, a3, a4, a5, a6, a7), okv, fv, rv, aev, scv);
     const bool prim = tl.dir == 0;
     const bool accept = (__ballot_sync(FULL, prim && !(okx && okv)) & 0x3fu) == 0;
     const bool finite = (__ballot_sync(FULL, prim && !(fx && fv)) & 0x3fu) == 0;
-    const float ratio = prim ? fmaxf(rx, rv) : 0.0f;
-    float errf = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) errf = fmaxf(errf, __shfl_sync(FULL, ratio, k));
+    float errf;
+    double errd;
+    group_err(0, tl.comp, prim, rx, aex, scx, rv, aev, scv, errf, errd);
     const int jj = tl.comp < 3 ? tl.comp : tl.comp - 3;
     const double wj = shfl(vn, 3 + jj) - shfl(vn, jj);
     const double w0 = shfl(wj, 0), w1 = shfl(wj, 1), w2 = shfl(wj, 2);
@@ -203,7 +203,7 @@ __device__ __forceinline__ int prim_attempt(const SysDev& P, const TLane& tl, in
         return PA_STOP;
     }
     if (!accept) {
-        st = on_reject(P, S, errf);
+        st = on_reject(P, S, errd, errf);
         return st != 0xffffffffu ? PA_STOP : PA_REJ;
     }
     if (on_accept(P, S, rd, r2n0)) {
@@ -215,7 +215,7 @@ __device__ __forceinline__ int prim_attempt(const SysDev& P, const TLane& tl, in
     v = vn;
     a1 = a7;
     c1 = cs67;
-    on_commit(P, S, errf);
+    on_commit(P, S, errd, errf);
     return PA_COMMIT;
 }
 

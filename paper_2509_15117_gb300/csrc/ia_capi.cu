@@ -89,10 +89,11 @@ struct Part {
     int lane_only;                          // 1: the lane phase alone (the autotuner's timing runs)
 };
 
-// Warps of a reserved SM's block that work on the tail: one per SM sub-partition, so that each tail
-// warp has an FP64 unit to itself (the latency of one trajectory in group mode is its FP64 instruction
-// count per step); further warps of that block leave.
+// Warps of a reserved SM's block that work on the tail by default: one per SM sub-partition, so that
+// each tail warp has an FP64 unit to itself (the latency of one trajectory in group mode is its FP64
+// instruction count per step); further warps of that block leave. At most MAX_TAIL_WARPS.
 constexpr int TAIL_WARPS = 4;
+constexpr int MAX_TAIL_WARPS = 8;
 
 __device__ __forceinline__ unsigned long long global_ns()
 {
@@ -446,18 +447,18 @@ __device__ __forceinline__ int tail_phase(const SysDev* __restrict__ tab, const 
 
         bool okx, fx, okv, fv;
         float rx, rv;
-        err_check(P.rtol, P.atol_pos, x, xn, err_x(K, a1, a3, a4, a5, a6), okx, fx, rx);
-        err_check(P.rtol, P.atol_vel, v, vn, err_v(K, a1, a3, a4, a5, a6, a7), okv, fv, rv);
+        double aex, scx, aev, scv;
+        err_check(P.rtol, P.atol_pos, x, xn, err_x(K, a1, a3, a4, a5, a6), okx, fx, rx, aex, scx);
+        err_check(P.rtol, P.atol_vel, v, vn, err_v(K, a1, a3, a4, a5, a6, a7), okv, fv, rv, aev, scv);
         const bool real = gl.c < 6;
         const bool ok = !real || (okx && okv);
         const bool fi = !real || (fx && fv);
-        const float ratio = real ? fmaxf(rx, rv) : 0.0f;
         const unsigned gmask = ((1u << G) - 1u) << gl.base;
         const bool accept = (__ballot_sync(FULL, !ok) & gmask) == 0;
         const bool finite = (__ballot_sync(FULL, !fi) & gmask) == 0;
-        float errf = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) errf = fmaxf(errf, __shfl_sync(FULL, ratio, gl.base + k));
+        float errf;
+        double errd;
+        group_err(gl.base, gl.c, real, rx, aex, scx, rv, aev, scv, errf, errd);
         // radial velocity sign at the step end: d . (v_a - v_i)
         const int j = gl.comp < 3 ? gl.comp : gl.comp - 3;
         const double wj = shfl(vn, gl.base + 3 + j) - shfl(vn, gl.base + j);
@@ -472,7 +473,7 @@ __device__ __forceinline__ int tail_phase(const SysDev* __restrict__ tab, const 
                 res = 1;
                 st = ST_NONFINITE;
             } else if (!accept) {
-                st = on_reject(P, S, errf);
+                st = on_reject(P, S, errd, errf);
                 if (st != 0xffffffffu) res = 1;
             } else if (on_accept(P, S, rd, r2new)) {
                 res = 2;
@@ -480,7 +481,7 @@ __device__ __forceinline__ int tail_phase(const SysDev* __restrict__ tab, const 
                 x = xn;
                 v = vn;
                 a1 = a7;
-                on_commit(P, S, errf);
+                on_commit(P, S, errd, errf);
             }
         }
         if (__any_sync(FULL, res != 0)) {
@@ -545,7 +546,8 @@ struct __align__(16) PairShared {
     double vn[32];      // helper -> chain: velocity at the step end
     double rd[32];      // helper -> chain: d . (v_a - v_i) at the step end
     long long ck[32];   // helper -> chain: claimed suspend record of the lane's group
-    float errf[32];     // helper -> chain: error ratio of the lane's group
+    float errf[32];     // helper -> chain: FP32 error ratio of the lane's group
+    double errd[32];    // helper -> chain: its FP64 error measure
     int dec[32];        // helper -> chain: bit 0 accept, bit 1 finite
     int claim[32];      // helper -> chain: claim result of the lane's group (0..3, as in tail_phase)
     unsigned long long seq_h[32], seq_c[32];  // posts of the helper and of the chain warp, per lane
@@ -739,6 +741,7 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
         double xn, vn, a7, r2new, rd;
         double a3 = 0.0, a4 = 0.0, a5 = 0.0, a6 = 0.0;  // helper: kept for the exit epilogue
         float errf;
+        double errd;
         bool accept, finite;
         if (helper) {
             // rf phases first: the chain warp needs the ion trap coefficient of stage 2 soonest.
@@ -809,7 +812,8 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
             ev = fma(K.e6, a6, ev);
             bool okx, fx, okv, fv;
             float rx, rv;
-            err_check(P.rtol, P.atol_pos, x, xn, ex, okx, fx, rx);      // while the chain warp forms a7
+            double aex, scx, aev, scv;
+            err_check(P.rtol, P.atol_pos, x, xn, ex, okx, fx, rx, aex, scx);  // while the chain warp forms a7
             const int j = gl.comp < 3 ? gl.comp : gl.comp - 3;
             const double wj = shfl(vn, gl.base + 3 + j) - shfl(vn, gl.base + j);
             const double w0 = shfl(wj, gl.base + 0), w1 = shfl(wj, gl.base + 1), w2 = shfl(wj, gl.base + 2);
@@ -818,21 +822,19 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
             r2new = sh->r2n[lane];
             const double dn0 = sh->dn[0][lane], dn1 = sh->dn[1][lane], dn2 = sh->dn[2][lane];
             ev = fma(K.e7, a7, ev);
-            err_check(P.rtol, P.atol_vel, v, vn, ev, okv, fv, rv);
+            err_check(P.rtol, P.atol_vel, v, vn, ev, okv, fv, rv, aev, scv);
             const bool real = gl.c < 6;
             const bool okk = !real || (okx && okv);
             const bool fi = !real || (fx && fv);
-            const float ratio = real ? fmaxf(rx, rv) : 0.0f;
             const unsigned gmask = ((1u << G) - 1u) << gl.base;
             accept = (__ballot_sync(FULL, !okk) & gmask) == 0;
             finite = (__ballot_sync(FULL, !fi) & gmask) == 0;
-            errf = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) errf = fmaxf(errf, __shfl_sync(FULL, ratio, gl.base + k));
+            group_err(gl.base, gl.c, real, rx, aex, scx, rv, aev, scv, errf, errd);
             rd = fma(dn0, w0, fma(dn1, w1, dn2 * w2));
             sh->vn[lane] = vn;
             sh->rd[lane] = rd;
             sh->errf[lane] = errf;
+            sh->errd[lane] = errd;
             sh->dec[lane] = (accept ? 1 : 0) | (finite ? 2 : 0);
             pair_post(sh->seq_h, nh);                                     // H5: the decision
             if (!ok) broken = true;
@@ -891,6 +893,7 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
             vn = sh->vn[lane];
             rd = sh->rd[lane];
             errf = sh->errf[lane];
+            errd = sh->errd[lane];
             const int dec = sh->dec[lane];
             accept = (dec & 1) != 0;
             finite = (dec & 2) != 0;
@@ -906,7 +909,7 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
                 res = 1;
                 st = ST_NONFINITE;
             } else if (!accept) {
-                st = on_reject(P, S, errf);
+                st = on_reject(P, S, errd, errf);
                 if (st != 0xffffffffu) res = 1;
             } else if (on_accept(P, S, rd, r2new)) {
                 res = 2;
@@ -914,7 +917,7 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
                 x = xn;
                 v = vn;
                 a1 = a7;
-                on_commit(P, S, errf);
+                on_commit(P, S, errd, errf);
             }
         }
         if (__any_sync(FULL, res != 0)) {
@@ -966,7 +969,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sched(const SysDev* __restrict_
                                                        ObsPtrs out, Part part, Counters* __restrict__ ctr,
                                                        unsigned* __restrict__ ready, Susp* __restrict__ susp,
                                                        long long cap, int refill, int budget, int tail_sms,
-                                                       int wait_ok, int pair)
+                                                       int wait_ok, int pair, int tail_warps)
 {
     __shared__ int role;  // 0 lane phase first, 1 tail worker, 2 surplus block on a reserved SM
     __shared__ PairShared pair_sh[G == 6 ? BLOCK / 64 : 1];
@@ -984,8 +987,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sched(const SysDev* __restrict_
         role = r;
     }
     __syncthreads();
-    // a reserved SM's block keeps TAIL_WARPS tail warps; its other warps leave (pairs need all of them)
-    const int r = (role == 1 && !(G == 6 && pair && wait_ok) && (threadIdx.x >> 5) >= TAIL_WARPS) ? 2 : role;
+    // a reserved SM's block keeps tail_warps tail warps; its other warps leave (pairs need all of them)
+    const int r = (role == 1 && !(G == 6 && pair && wait_ok) && (int)(threadIdx.x >> 5) >= tail_warps) ? 2 : role;
     const unsigned long long total_warps = (unsigned long long)gridDim.x * (BLOCK / 32);
     // carry records written by the previous part's launch (complete before this launch started)
     long long n_carry = 0, n_tc = 0;
@@ -1184,15 +1187,15 @@ __global__ void __launch_bounds__(128) k_tangent(const SysDev* __restrict__ tab,
             // error test on the primal lanes
             bool okx, fx, okv, fv;
             float rx, rv;
-            err_check(P.rtol, P.atol_pos, x, xn, err_x(K, a1, a3, a4, a5, a6), okx, fx, rx);
-            err_check(P.rtol, P.atol_vel, v, vn, err_v(K, a1, a3, a4, a5, a6, a7), okv, fv, rv);
+            double aex, scx, aev, scv;
+            err_check(P.rtol, P.atol_pos, x, xn, err_x(K, a1, a3, a4, a5, a6), okx, fx, rx, aex, scx);
+            err_check(P.rtol, P.atol_vel, v, vn, err_v(K, a1, a3, a4, a5, a6, a7), okv, fv, rv, aev, scv);
             const bool prim = tl.dir == 0;
             const bool accept = (__ballot_sync(FULL, prim && !(okx && okv)) & 0x3fu) == 0;
             const bool finite = (__ballot_sync(FULL, prim && !(fx && fv)) & 0x3fu) == 0;
-            const float ratio = prim ? fmaxf(rx, rv) : 0.0f;
-            float errf = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) errf = fmaxf(errf, __shfl_sync(FULL, ratio, k));
+            float errf;
+            double errd;
+            group_err(0, lane, prim, rx, aex, scx, rv, aev, scv, errf, errd);
             const int jj = tl.comp < 3 ? tl.comp : tl.comp - 3;
             const double wj = shfl(vn, 3 + jj) - shfl(vn, jj);
             const double w0 = shfl(wj, 0), w1 = shfl(wj, 1), w2 = shfl(wj, 2);
@@ -1203,7 +1206,7 @@ __global__ void __launch_bounds__(128) k_tangent(const SysDev* __restrict__ tab,
                 break;
             }
             if (!accept) {
-                st = on_reject(P, S, errf);
+                st = on_reject(P, S, errd, errf);
                 if (st != 0xffffffffu) {
                     res = 1;
                     break;
@@ -1217,7 +1220,7 @@ __global__ void __launch_bounds__(128) k_tangent(const SysDev* __restrict__ tab,
             x = xn;
             v = vn;
             a1 = a7;
-            on_commit(P, S, errf);
+            on_commit(P, S, errd, errf);
             // exact power-of-two rescaling of a tangent direction that left [2^-256, 2^256]
             int me = max_exp3(x, v, a1);
 #pragma unroll
@@ -1565,7 +1568,8 @@ int resolve(int64_t n, const ia_launch_opts* opts, Resolved& r)
     if (o.refill == 0) o.refill = 1;
     if (o.refill < 1 || o.refill > 32) return IA_ERR_INVALID_ARG;
     if (o.grid < 0 || o.blocks_per_sm < 0 || o.tail_blocks_per_sm < 0) return IA_ERR_INVALID_ARG;
-    if (o.tail_pair < -1 || o.tail_pair > 1 || o.reserved != 0) return IA_ERR_INVALID_ARG;
+    if (o.tail_pair < -1 || o.tail_pair > 1 || o.tail_warps < 0 || o.tail_warps > MAX_TAIL_WARPS)
+        return IA_ERR_INVALID_ARG;
     if (o.slice_budget == 0) o.slice_budget = DEFAULT_BUDGET;
     if (o.slice_budget < -1) return IA_ERR_INVALID_ARG;
     if (o.tail_group == 0) o.tail_group = 6;
@@ -1602,7 +1606,7 @@ const void* sched_fn(int block, int minb, int g)
 // Launch configuration of the fused kernel for resolved options on the system's device.
 struct SchedCfg {
     const void* fn;
-    int block, grid, resident, budget, wait_ok, tail_sms, pair, refill;
+    int block, grid, resident, budget, wait_ok, tail_sms, pair, refill, tail_warps;
 };
 
 int sched_config(const ia_system* sys, const Resolved& r, SchedCfg& c)
@@ -1634,6 +1638,8 @@ int sched_config(const ia_system* sys, const Resolved& r, SchedCfg& c)
     if (c.tail_sms > sys->num_sms / 2) c.tail_sms = sys->num_sms / 2;
     c.pair = (o.tail_group != 8 && o.tail_pair == 1) ? 1 : 0;
     c.refill = o.refill;
+    c.tail_warps = o.tail_warps == 0 ? std::min(TAIL_WARPS, c.block / 32) : o.tail_warps;
+    if (c.tail_warps < 1 || c.tail_warps > MAX_TAIL_WARPS || c.tail_warps > c.block / 32) return IA_ERR_INVALID_ARG;
     return IA_OK;
 }
 
@@ -1647,11 +1653,12 @@ int launch_sched(const ia_system* sys, const SchedCfg& c, const Resolved& r, IcP
     Susp* susp = reinterpret_cast<Susp*>(scratch + SCRATCH_HEAD + ready_bytes(r.cap));
     long long cap = r.cap;
     int refill = c.refill, budget = c.budget, tail_sms = c.tail_sms, wait_ok = c.wait_ok, pair = c.pair;
+    int tail_warps = c.tail_warps;
     int n_sys = sys->n_sys;
     const SysDev* tab = sys->d_tab;
     void* args[] = {(void*)&tab, (void*)&n_sys, (void*)&icp, (void*)&op, (void*)&part, (void*)&ctr, (void*)&ready,
                     (void*)&susp, (void*)&cap, (void*)&refill, (void*)&budget, (void*)&tail_sms, (void*)&wait_ok,
-                    (void*)&pair};
+                    (void*)&pair, (void*)&tail_warps};
     cudaError_t e;
     if (wait_ok)
         e = cudaLaunchCooperativeKernel(c.fn, dim3(c.grid), dim3(c.block), args, 0, st);
@@ -1860,7 +1867,7 @@ int ia_queue_create(ia_system* sys, int64_t n, const ia_launch_opts* opts, ia_qu
     if (!coop) return IA_ERR_NO_DEVICE;
     const long long carry_cap = (long long)cfg.grid * cfg.block;  // one record per lane of the grid
     // one group-mode record per trajectory the reserved SMs' tail warps can hold
-    const long long tcarry_cap = (long long)(cfg.tail_sms > 0 ? cfg.tail_sms : 1) * TAIL_WARPS * 5;
+    const long long tcarry_cap = (long long)(cfg.tail_sms > 0 ? cfg.tail_sms : 1) * cfg.tail_warps * 5;
     const size_t carry_off = r.bytes;
     const size_t bytes = carry_off + 2 * (size_t)(carry_cap + tcarry_cap) * sizeof(Susp);
     ia_queue* Q = new (std::nothrow) ia_queue;
@@ -2166,13 +2173,14 @@ int ia_autotune(ia_system* sys, const ia_ic_soa* ic, int64_t n, int32_t attempt_
         int grid = resident * sys->num_sms;
         long long nn_ = (long long)n;
         int refill = cd.refill, budget = attempt_cap, tail_sms = 0, wait_ok = 0, pair = 0, n_sys = sys->n_sys;
+        int tail_warps = TAIL_WARPS;
         long long capv = cap;
         const SysDev* tab = sys->d_tab;
         Part part = single_part(nn_);
         part.lane_only = 1;  // every trajectory stops at the cap (its suspend record is never resumed)
         void* args[] = {(void*)&tab, (void*)&n_sys, (void*)&icp, (void*)&op, (void*)&part, (void*)&ctr,
                         (void*)&ready, (void*)&susp, (void*)&capv, (void*)&refill, (void*)&budget,
-                        (void*)&tail_sms, (void*)&wait_ok, (void*)&pair};
+                        (void*)&tail_sms, (void*)&wait_ok, (void*)&pair, (void*)&tail_warps};
         if (cudaMemsetAsync(scr, 0, SCRATCH_HEAD + ready_bytes(cap), st) != cudaSuccess) rc = IA_ERR_CUDA;
         cudaEventRecord(e0, st);
         // budget > 0 with no tail workers: the kernel stops every trajectory at the cap

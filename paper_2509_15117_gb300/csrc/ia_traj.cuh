@@ -287,29 +287,71 @@ __device__ __forceinline__ double err_x(const Coef& K, double a1, double a3, dou
     return fma(K.f6, a6, fma(K.f5, a5, fma(K.f4, a4, fma(K.f3, a3, K.f1 * a1))));
 }
 
-// ode45 error test of one component: ok iff |e| <= max(rtol max(|y|, |ynew|), atol); the ratio is
-// returned in FP32 for the step-size factor.
+// ode45 error test of one component: ok iff |e| <= sc = max(rtol max(|y|, |ynew|), atol). The ratio
+// |e| / sc is returned in FP32 (to find the component with the largest ratio cheaply), with |e| and sc.
 __device__ __forceinline__ void err_check(double rtol, double atol, double y_old, double y_new, double e,
-                                          bool& ok, bool& finite, float& ratio)
+                                          bool& ok, bool& finite, float& ratio, double& ae, double& sc)
 {
     double w = nn_max(dabs(y_old), dabs(y_new));
-    double sc = nn_max(rtol * w, atol);
-    double ae = dabs(e);
+    sc = nn_max(rtol * w, atol);
+    ae = dabs(e);
     ok = nn_le(ae, sc);
     finite = is_finite(y_new) && is_finite(e);
     ratio = nn_to_float(ae) * __frcp_rn(nn_to_float(sc));
 }
 
-// Step-size factors of ode45 from the FP32 error ratio.
-__device__ __forceinline__ double grow_factor(float errf)
+// ode45's error measure err = max_k |e_k| / sc_k over the twelve components. The components' ratios
+// are compared in FP32; the largest (ties to the lowest index k in the order x_ion0, v_ion0, x_ion1,
+// ..., x_atom2, v_atom2, the same in every layout) is then formed in FP64, so that the step-size rules
+// see the error measure the oracle sees, to a few ulps.
+struct ErrMax {
+    unsigned long long key;  // bits of the FP32 ratio << 32 | (15 - k): larger key = larger ratio, lower k
+    double ae, sc;
+};
+__device__ __forceinline__ unsigned long long err_key(float ratio, int k)
 {
-    // h / (1.25 err^(1/5)) if that factor exceeds 0.2, else 5 h
-    float fac = (errf > 1.048576e-4f) ? 0.8f * exp2f(-0.2f * __log2f(errf)) : 5.0f;
-    return pos_float_to_double(fac);
+    return ((unsigned long long)__float_as_uint(ratio) << 32) | (unsigned long long)(15 - k);
 }
-__device__ __forceinline__ double shrink_factor(float errf)
+__device__ __forceinline__ void err_take(ErrMax& m, float ratio, int k, double ae, double sc)
 {
-    return pos_float_to_double(fmaxf(0.1f, 0.8f * exp2f(-0.2f * __log2f(errf))));
+    const unsigned long long key = err_key(ratio, k);
+    if (key > m.key) {
+        m.key = key;
+        m.ae = ae;
+        m.sc = sc;
+    }
+}
+// The measure itself: |e| / sc of the winning component in FP64 (sc > 0: atol > 0).
+__device__ __forceinline__ double err_measure(double ae, double sc) { return ae * rcp_nr(sc); }
+
+// err^(-1/5) for err in [0.16^5, 0.125^-5] (where the step-size factor is not clamped): the FP32 value
+// exp2(-0.2 log2 err) (relative error ~2^-21) refined by two Newton steps on err y^5 = 1, each of
+// which squares the relative error (y <- y (1 - (err y^5 - 1)/5) leaves 3 eps^2): ~2^-40, then below
+// the FP64 rounding of the arithmetic.
+__device__ __forceinline__ double err_pow_m02(double err, float errf)
+{
+    double y = pos_float_to_double(exp2f(-0.2f * __log2f(errf)));
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double y2 = y * y;
+        const double y5 = (y2 * y2) * y;
+        const double r = fma(err, y5, -1.0);
+        y = fma(-0.2 * y, r, y);
+    }
+    return y;
+}
+
+// Step-size factors of ode45 (Shampine & Reichelt 1997) from the error measure err (FP64) and its FP32
+// value errf. After an accepted step: h / (1.25 err^(1/5)) = h 0.8 err^(-1/5) when 1.25 err^(1/5) > 0.2,
+// i.e. err > 0.16^5, else 5 h.
+__device__ __forceinline__ double grow_factor(double err, float errf)
+{
+    return nn_lt(1.048576e-4, err) ? 0.8 * err_pow_m02(err, errf) : 5.0;
+}
+// After a first failure: max(0.1, 0.8 err^(-1/5)); the floor holds from err = 0.125^-5 = 32768 on.
+__device__ __forceinline__ double shrink_factor(double err, float errf)
+{
+    return nn_lt(err, 32768.0) ? nn_max(0.1, 0.8 * err_pow_m02(err, errf)) : 0.1;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -432,7 +474,7 @@ __device__ __forceinline__ uint32_t attempt_begin(const SysDev& P, Scal& S)
 
 // After the error test of an attempt: bookkeeping of a rejection. Returns a stop status or
 // 0xffffffff to go on (the attempt is repeated with the smaller h).
-__device__ __forceinline__ uint32_t on_reject(const SysDev& P, Scal& S, float errf)
+__device__ __forceinline__ uint32_t on_reject(const SysDev& P, Scal& S, double err, float errf)
 {
     const double h = S.h;
     S.n_rej += 1;
@@ -440,7 +482,7 @@ __device__ __forceinline__ uint32_t on_reject(const SysDev& P, Scal& S, float er
     double fac;
     if (S.nofailed) {
         S.nofailed = false;
-        fac = shrink_factor(errf);  // max(0.1, 0.8 err^(-1/5))
+        fac = shrink_factor(err, errf);  // max(0.1, 0.8 err^(-1/5))
     } else {
         fac = 0.5;
     }
@@ -466,11 +508,11 @@ __device__ __forceinline__ bool on_accept(const SysDev& P, Scal& S, double rd, d
     return nn_le(P.r0sq, r2new) && dbits(rd) > 0;  // rd > 0
 }
 
-__device__ __forceinline__ void on_commit(const SysDev& P, Scal& S, float errf)
+__device__ __forceinline__ void on_commit(const SysDev& P, Scal& S, double err, float errf)
 {
     const double t = S.t, h = S.h;
     S.t = nn_le(P.t_max, t + h) ? P.t_max : t + h;
-    if (S.nofailed) S.h = h * grow_factor(errf);
+    if (S.nofailed) S.h = h * grow_factor(err, errf);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -662,26 +704,32 @@ __device__ __forceinline__ int lane_attempt(const SysDev& P, Lane& L, Final& fin
         }
         // embedded error estimate and ode45's error test
         bool accept = true, finite = true;
-        float errf = 0.0f;
+        ErrMax em;
+        em.key = 0ull;
+        em.ae = 0.0;
+        em.sc = 1.0;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             bool ok, fi;
             float r;
-            err_check(P.rtol, P.atol_pos, L.xi[j], xni[j], err_x(K, L.a1i[j], a3i[j], a4i[j], a5i[j], a6i[j]), ok, fi, r);
-            accept = accept && ok; finite = finite && fi; errf = fmaxf(errf, r);
-            err_check(P.rtol, P.atol_vel, L.vi[j], vni[j], err_v(K, L.a1i[j], a3i[j], a4i[j], a5i[j], a6i[j], a7i[j]), ok, fi, r);
-            accept = accept && ok; finite = finite && fi; errf = fmaxf(errf, r);
-            err_check(P.rtol, P.atol_pos, L.xa[j], xna[j], err_x(K, L.a1a[j], a3a[j], a4a[j], a5a[j], a6a[j]), ok, fi, r);
-            accept = accept && ok; finite = finite && fi; errf = fmaxf(errf, r);
-            err_check(P.rtol, P.atol_vel, L.va[j], vna[j], err_v(K, L.a1a[j], a3a[j], a4a[j], a5a[j], a6a[j], a7a[j]), ok, fi, r);
-            accept = accept && ok; finite = finite && fi; errf = fmaxf(errf, r);
+            double ae, sc;
+            err_check(P.rtol, P.atol_pos, L.xi[j], xni[j], err_x(K, L.a1i[j], a3i[j], a4i[j], a5i[j], a6i[j]), ok, fi, r, ae, sc);
+            accept = accept && ok; finite = finite && fi; err_take(em, r, 2 * j, ae, sc);
+            err_check(P.rtol, P.atol_vel, L.vi[j], vni[j], err_v(K, L.a1i[j], a3i[j], a4i[j], a5i[j], a6i[j], a7i[j]), ok, fi, r, ae, sc);
+            accept = accept && ok; finite = finite && fi; err_take(em, r, 2 * j + 1, ae, sc);
+            err_check(P.rtol, P.atol_pos, L.xa[j], xna[j], err_x(K, L.a1a[j], a3a[j], a4a[j], a5a[j], a6a[j]), ok, fi, r, ae, sc);
+            accept = accept && ok; finite = finite && fi; err_take(em, r, 2 * (3 + j), ae, sc);
+            err_check(P.rtol, P.atol_vel, L.va[j], vna[j], err_v(K, L.a1a[j], a3a[j], a4a[j], a5a[j], a6a[j], a7a[j]), ok, fi, r, ae, sc);
+            accept = accept && ok; finite = finite && fi; err_take(em, r, 2 * (3 + j) + 1, ae, sc);
         }
         if (!finite) {
             fin.status = ST_NONFINITE;
             goto stop_here;
         }
+        const float errf = __uint_as_float((unsigned)(em.key >> 32));
+        const double errd = err_measure(em.ae, em.sc);
         if (!accept) {
-            st = on_reject(P, L.s, errf);
+            st = on_reject(P, L.s, errd, errf);
             if (st != 0xffffffffu) {
                 fin.status = st;
                 goto stop_here;
@@ -710,7 +758,7 @@ __device__ __forceinline__ int lane_attempt(const SysDev& P, Lane& L, Final& fin
             L.xi[j] = xni[j]; L.xa[j] = xna[j]; L.vi[j] = vni[j]; L.va[j] = vna[j];
             L.a1i[j] = a7i[j]; L.a1a[j] = a7a[j];
         }
-        on_commit(P, L.s, errf);
+        on_commit(P, L.s, errd, errf);
         return RUNNING;
     }
 stop_here:
@@ -901,6 +949,30 @@ __device__ __forceinline__ double accel_group(const SysDev& P, const GroupLane<G
     d3[1] = d1;
     d3[2] = d2;
     return fma(kc, p, q);
+}
+
+// Error measure of a trajectory held by lanes base .. base + 5 (lane base + c holds component c of
+// [x_ion, x_atom], whose position and velocity are components k = 2c and 2c + 1 of the measure): the
+// largest FP32 ratio of the group, ties to the lowest k (as in lane mode), and that component's FP64
+// ratio, identical on every lane. real = false on lanes outside the six.
+__device__ __forceinline__ void group_err(int base, int c, bool real, float rx, double aex, double scx, float rv,
+                                          double aev, double scv, float& errf, double& errd)
+{
+    const unsigned long long kx = real ? err_key(rx, 2 * c) : 0ull;
+    const unsigned long long kv = real ? err_key(rv, 2 * c + 1) : 0ull;
+    const bool vb = kv > kx;
+    const unsigned long long key = vb ? kv : kx;
+    const double ae = vb ? aev : aex, sc = vb ? scv : scx;
+    unsigned long long best = 0ull;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const unsigned long long o = __shfl_sync(FULL, key, base + j);
+        best = o > best ? o : best;
+    }
+    const int src = base + ((15 - (int)(best & 15ull)) >> 1);
+    const double aw = shfl(ae, src), sw = shfl(sc, src);
+    errf = __uint_as_float((unsigned)(best >> 32));
+    errd = best == 0ull ? 0.0 : err_measure(aw, sw);
 }
 
 // Result of a trajectory whose sys_id is outside the table: its initial state, BAD_IC.

@@ -1,15 +1,43 @@
 """Parity criteria between the CUDA path and the CPU oracle (test helper).
 
 Conditioning of the observables. The ion-atom bounce amplifies perturbations of the state by about
-10^7 even on single-bounce (non-complex) trajectories: a 1e-15 relative change of the initial atom
-position moves t_f by ~1e-8 and the outgoing atom velocity by ~1e-7 relative, in the oracle and in an
-independent 8th-order integrator alike. Two correct FP64 implementations that round in different
-orders therefore disagree at that level. Per trajectory the bar is
-    |gpu - oracle| <= max(1e-8 |oracle|, K * spread),
-where `spread` is the oracle's own response to three ulp-level perturbations of the input (the noise
-floor of FP64 for that trajectory and observable; a few samples can underestimate it, so it is
-floored at the batch median of spread/|value| times |value|) and K = 30. The fraction of trajectories
-that meet the plain 1e-8 relative bar is reported alongside.
+10^7 (10^8 at 1.5 uK) even on single-bounce (non-complex) trajectories, so two correct FP64
+implementations that round in different orders disagree far above 1e-16 there: the GPU forms the DP5
+stages in Nystrom form and rounds differently from the oracle's textbook tableau at every step. Each
+trajectory's own FP64 noise floor is measured on the oracle side:
+
+    spread = max |oracle' - oracle| over nine runs of the oracle: three with the initial state moved by
+             ulps (atom position, atom velocity, rf phase) and six under the oracle's rounding-noise
+             model (every component moved by up to 1 ulp after every accepted step, six seeds).
+
+Bars, on trajectories that end with one bounce on both sides (the regular, non-complex trajectories):
+  - well-conditioned (spread < 1e-9 |oracle|): |gpu - oracle| <= 1e-8 |oracle| (the plain bar);
+  - every trajectory: |gpu - oracle| <= max(1e-8 |oracle|, 16 spread);
+  - all but a fraction 0.002 (the maximum of nine runs underestimates a heavy-tailed noise now and
+    then): |gpu - oracle| <= max(1e-8 |oracle|, 4 spread);
+  - distribution: the GPU's differences are distributed like the oracle's own differences under the
+    noise model (median and 90th percentile of log10 |diff|/|oracle| within 0.5 of each other), so a
+    systematic error hiding under the per-trajectory bars shows as a shift (checked where the
+    differences are not all a hundred times below the plain bar: the bounce times differ by ~1e-12
+    because the GPU forms the step-size factor in FP32, which the noise model does not imitate);
+  - n_bounce is 1 on the GPU wherever the oracle's is 1 and none of the nine runs changes it; the
+    complex flag may flip only on trajectories where the oracle's own runs flip it (at most twice their
+    count plus two).
+The step sequence. Both sides apply ode45's step-size rules in FP64, but to error estimates that round
+differently: the estimate is a difference of O(h) terms (a tiny remainder of large ones), and the GPU
+sums it in Nystrom form, so its rounding leaves the two estimates ~1e-8 apart in relative terms. Step
+sizes that are not clamped to h_max inherit a fifth of that. Two consequences are allowed for:
+  - once in a while an error ratio lies within that distance of the accept/reject boundary and the two
+    sides take different step sequences; their results then differ by discretization error, not
+    rounding. At least 99% of single-bounce trajectories must take the identical sequence (same
+    accepted and rejected counts), and the per-trajectory bars above apply to those;
+  - the bounce times are stamped at the end of the step that contains the pericentre, on the step grid,
+    which those step sizes move (the controller corrects a step that came out long or short at the next
+    step, so the shift does not accumulate): they are held to max(2^-20 |oracle|, 4 spread) instead of
+    1e-8 |oracle|. Head-on runs, whose approach steps sit at h_max, agree to ~1e-12; thermal runs with a
+    moving ion, to ~1e-8 on about 90% of trajectories.
+Fields: theta_s, dp, dE_ion, t_final, t_first_bounce, t_last_bounce and, when both sides provide it,
+the final state (per particle position and velocity, as vector norms).
 """
 from __future__ import annotations
 
@@ -19,61 +47,127 @@ import numpy as np
 
 from oracle import oracle as O
 
-FIELDS = ("theta_s", "dp", "dE_ion", "t_final")
-K_SPREAD = 30.0
+FIELDS = ("theta_s", "dp", "dE_ion", "t_final", "t_first_bounce", "t_last_bounce")
+GRID_FIELDS = ("t_first_bounce", "t_last_bounce")  # stamped on the step grid
 REL = 1e-8
+GRID_REL = 2.0 ** -20
+K_SPREAD = 4.0
+K_HARD = 16.0
+OUTLIER_FRAC = 0.002
+WELL = 1e-9
+NOISE_SEEDS = (101, 102, 103, 104, 105, 106)
+BLOCKS = ((0, 3), (3, 6), (6, 9), (9, 12))  # ion position, ion velocity, atom position, atom velocity
 
 
 def oracle_with_spread(systems, y0, phi0, sys_id, nthreads=0):
-    """Oracle results plus the per-trajectory spread under two ulp-level input perturbations."""
+    """Oracle results plus each trajectory's FP64 noise floor (see the module docstring)."""
+    y0 = np.asarray(y0, dtype=np.float64)
+    phi0 = np.asarray(phi0, dtype=np.float64)
     base = O.run_batch(systems, y0, phi0, sys_id, nthreads=nthreads)
-    ya = np.array(y0, dtype=np.float64, copy=True)
+    runs = []
+    ya = np.array(y0, copy=True)
     ya[:, 6:9] *= 1.0 + 2.0 ** -51
-    pa = O.run_batch(systems, ya, phi0, sys_id, nthreads=nthreads)
-    yb = np.array(y0, dtype=np.float64, copy=True)
+    runs.append(O.run_batch(systems, ya, phi0, sys_id, nthreads=nthreads))
+    yb = np.array(y0, copy=True)
     yb[:, 9:12] *= 1.0 - 2.0 ** -51
-    pb = O.run_batch(systems, yb, phi0, sys_id, nthreads=nthreads)
-    pc = O.run_batch(systems, y0, np.asarray(phi0, dtype=np.float64) + 2.0 ** -50, sys_id, nthreads=nthreads)
-    spread = {}
-    single = base["n_bounce"] == 1
-    for f in FIELDS:
-        s = np.maximum.reduce([np.abs(pa[f] - base[f]), np.abs(pb[f] - base[f]), np.abs(pc[f] - base[f])])
-        if single.any():
-            rel = s[single] / np.maximum(np.abs(base[f][single]), 1e-300)
-            s = np.maximum(s, float(np.median(rel)) * np.abs(base[f]))
-        spread[f] = s
+    runs.append(O.run_batch(systems, yb, phi0, sys_id, nthreads=nthreads))
+    runs.append(O.run_batch(systems, y0, phi0 + 2.0 ** -50, sys_id, nthreads=nthreads))
+    noise = [O.run_batch(systems, y0, phi0, sys_id, nthreads=nthreads, noise_seed=s, noise_ulps=1)
+             for s in NOISE_SEEDS]
+    runs += noise
+    spread = {f: np.max([np.abs(r[f] - base[f]) for r in runs], axis=0) for f in FIELDS}
+    spread["y_final"] = np.max([block_norms(r["y_final"] - base["y_final"]) for r in runs], axis=0)
+    spread["nb_changed"] = np.any([r["n_bounce"] != base["n_bounce"] for r in runs], axis=0)
+    spread["flip_any"] = np.any([(r["n_bounce"] >= 2) != (base["n_bounce"] >= 2) for r in runs], axis=0)
+    spread["noise_sample"] = noise[0]
     return base, spread
 
 
-def compare(gpu: dict, orc: np.ndarray, spread: dict, max_flip: float = 0.03):
-    """Per-trajectory comparison on trajectories that are single-bounce on both sides.
-    Returns a report dict; raises AssertionError on failure."""
+def block_norms(y):
+    """(n, 12) states -> (n, 4) norms of the ion and atom position and velocity vectors."""
+    y = np.asarray(y)
+    return np.stack([np.linalg.norm(y[:, a:b], axis=1) for a, b in BLOCKS], axis=1)
+
+
+def _check_field(name, g, o, s, o_noise, rep, rel=REL):
+    diff = np.abs(g - o)
+    mag = np.abs(o)
+    plain = diff <= rel * mag
+    well = s < WELL * mag
+    soft = diff <= np.maximum(rel * mag, K_SPREAD * s)
+    hard = diff <= np.maximum(rel * mag, K_HARD * s)
+    n = len(o)
+    rep[name + "_within_1e-8"] = float(np.mean(diff <= REL * mag)) if n else 1.0
+    rep[name + "_well_conditioned"] = float(np.mean(well)) if n else 0.0
+    rep[name + "_median_rel"] = float(np.median(diff / np.maximum(mag, 1e-300))) if n else 0.0
+    rep[name + "_beyond_4_spread"] = int(np.sum(~soft))
+    bad = np.where(well & ~plain)[0]
+    assert bad.size == 0, (name, "well-conditioned beyond 1e-8", bad[:10].tolist(), rep)
+    bad = np.where(~hard)[0]
+    assert bad.size == 0, (name, f"beyond {K_HARD} x spread", bad[:10].tolist(),
+                           (diff[bad] / np.maximum(s[bad], 1e-300))[:10].tolist(), rep)
+    assert np.sum(~soft) <= int(OUTLIER_FRAC * n), (name, f"beyond {K_SPREAD} x spread",
+                                                    np.where(~soft)[0][:10].tolist(), rep)
+    if n >= 100 and o_noise is not None and rel == REL and np.mean(diff <= 1e-2 * REL * mag) < 0.99:
+        # the GPU's differences against the oracle's own under the rounding-noise model (for fields whose
+        # differences are not all a hundred times below the plain bar: there a shift does not matter)
+        lg = np.log10(np.maximum(diff, 1e-300 + 1e-18 * mag) / np.maximum(mag, 1e-300))
+        ln = np.log10(np.maximum(np.abs(o_noise - o), 1e-300 + 1e-18 * mag) / np.maximum(mag, 1e-300))
+        dmed = float(np.median(lg) - np.median(ln))
+        d90 = float(np.percentile(lg, 90) - np.percentile(ln, 90))
+        rep[name + "_log10_shift_median_p90"] = (round(dmed, 3), round(d90, 3))
+        assert abs(dmed) <= 0.5 and abs(d90) <= 0.5, (name, "distribution shift", dmed, d90, rep)
+
+
+def compare(gpu: dict, orc: np.ndarray, spread: dict):
+    """Per-trajectory comparison (see the module docstring). Returns a report dict; raises
+    AssertionError on failure."""
     n = len(orc)
     nb_g = gpu["n_bounce"]
     nb_o = orc["n_bounce"]
-    single = (nb_g == 1) & (nb_o == 1) & (orc["status"] == 0) & (gpu["status"] == 0)
-    complex_g = nb_g >= 2
-    complex_o = nb_o >= 2
-    flip = float(np.mean(complex_g != complex_o)) if n else 0.0
-    rep = {"n": n, "n_single": int(single.sum()), "complex_flip_frac": flip}
-    assert flip <= max_flip, rep
-    for f in FIELDS:
-        g = gpu[f][single]
-        o = orc[f][single]
-        s = spread[f][single]
-        diff = np.abs(g - o)
-        tol = np.maximum(REL * np.abs(o), K_SPREAD * s)
-        bad = diff > tol
-        rep[f + "_within_1e-8"] = float(np.mean(diff <= REL * np.abs(o))) if len(o) else 1.0
-        rep[f + "_median_rel"] = float(np.median(diff / np.maximum(np.abs(o), 1e-300))) if len(o) else 0.0
-        assert not bad.any(), (f, int(bad.sum()), np.where(single)[0][bad][:10].tolist(),
-                               (diff[bad] / np.abs(o[bad]))[:10].tolist(), rep)
-    # same step sequence in the vast majority of single-bounce trajectories
+    clean_g = (gpu["status"] & 0xFF) == 0
+    clean_o = (orc["status"] & 0xFF) == 0
+    single = (nb_g == 1) & (nb_o == 1) & clean_g & clean_o
+    flip = (nb_g >= 2) != (nb_o >= 2)
+    self_flips = int(np.sum(spread["flip_any"]))
+    rep = {"n": n, "n_single": int(single.sum()), "complex_flips": int(flip.sum()),
+           "oracle_self_flips": self_flips}
+    assert flip.sum() <= 2 * self_flips + 2, rep
+    stable_single = (nb_o == 1) & ~spread["nb_changed"] & clean_o
+    assert np.all(nb_g[stable_single] == 1), ("n_bounce differs where the oracle's is stable at 1",
+                                               np.where(stable_single & (nb_g != 1))[0][:10].tolist(), rep)
+    # the same step sequence (accept/reject decisions) as the oracle
+    same = (gpu["n_steps"] == orc["n_steps"]) & (gpu["n_rej"] == orc["n_rej"])
     if single.any():
-        dstep = np.abs(gpu["n_steps"][single].astype(np.int64) - orc["n_steps"][single])
-        rep["steps_identical_frac"] = float(np.mean(dstep == 0))
-        assert np.mean(dstep <= 0.02 * orc["n_steps"][single]) >= 0.99, rep
+        rep["steps_identical_frac"] = float(np.mean(same[single]))
+        assert np.mean(same[single]) >= 0.99, rep
+    comp = single & same
+    rep["n_compared"] = int(comp.sum())
+    noise = spread.get("noise_sample")
+    for f in FIELDS:
+        _check_field(f, gpu[f][comp], orc[f][comp], spread[f][comp],
+                     noise[f][comp] if noise is not None else None, rep,
+                     rel=GRID_REL if f in GRID_FIELDS else REL)
+    if "y_final" in gpu and comp.any():
+        _check_state(gpu["y_final"][comp], orc["y_final"][comp], spread["y_final"][comp], rep)
     return rep
+
+
+def _check_state(g, o, s, rep):
+    """Final states of single-bounce trajectories: per particle position and velocity, the norm of the
+    difference against max(1e-8 |oracle vector|, K spread), with the bars of the scalar fields."""
+    d = block_norms(g - o)
+    m = block_norms(o)
+    for b, nm in enumerate(("x_ion", "v_ion", "x_atom", "v_atom")):
+        diff, mag, sp = d[:, b], m[:, b], s[:, b]
+        plain = diff <= REL * mag
+        well = sp < WELL * mag
+        soft = diff <= np.maximum(REL * mag, K_SPREAD * sp)
+        hard = diff <= np.maximum(REL * mag, K_HARD * sp)
+        rep["y_final_" + nm + "_within_1e-8"] = float(np.mean(plain))
+        assert np.all(plain[well]), ("y_final", nm, "well-conditioned beyond 1e-8", rep)
+        assert np.all(hard), ("y_final", nm, f"beyond {K_HARD} x spread", np.where(~hard)[0][:10].tolist(), rep)
+        assert np.sum(~soft) <= int(OUTLIER_FRAC * len(diff)), ("y_final", nm, f"beyond {K_SPREAD} x spread", rep)
 
 
 def two_proportion_z(k1, n1, k2, n2):
@@ -92,7 +186,6 @@ def statistics_agree(gpu: dict, orc: np.ndarray, seed: int = 0):
     z = two_proportion_z(kg, n, ko, n)
     rep = {"P_complex_gpu": kg / n, "P_complex_oracle": ko / n, "z": z}
     assert z < 3.0, rep
-    bins = np.arange(0, 24)
     hg = np.bincount(np.minimum(np.floor(np.log2(np.maximum(gpu["n_bounce"], 1))).astype(int), 23), minlength=24)
     ho = np.bincount(np.minimum(np.floor(np.log2(np.maximum(orc["n_bounce"], 1))).astype(int), 23), minlength=24)
     keep = (hg + ho) >= 5
@@ -112,5 +205,19 @@ def statistics_agree(gpu: dict, orc: np.ndarray, seed: int = 0):
     rep["mean_dE_gpu"] = float(dg.mean())
     rep["mean_dE_oracle"] = float(do.mean())
     assert abs(dg.mean() - do.mean()) <= 3.0 * sd + 1e-30, rep
-    del bins
+    return rep
+
+
+def lifetimes_agree(gpu: dict, orc: np.ndarray):
+    """Complex lifetimes (t_last_bounce - t_first_bounce of trajectories with two or more bounces, the
+    quantity of the paper's Fig. 2) drawn from the same distribution on both sides: two-sample
+    Kolmogorov-Smirnov test at p > 1e-3 (chaotic complexes differ one by one, their statistics may not)."""
+    from scipy import stats
+    tg = (gpu["t_last_bounce"] - gpu["t_first_bounce"])[gpu["n_bounce"] >= 2]
+    to = (orc["t_last_bounce"] - orc["t_first_bounce"])[orc["n_bounce"] >= 2]
+    res = stats.ks_2samp(tg, to)
+    rep = {"complexes_gpu": int(tg.size), "complexes_oracle": int(to.size), "ks_p": float(res.pvalue),
+           "median_lifetime_gpu": float(np.median(tg)) if tg.size else 0.0,
+           "median_lifetime_oracle": float(np.median(to)) if to.size else 0.0}
+    assert res.pvalue > 1e-3, rep
     return rep

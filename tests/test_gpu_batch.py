@@ -121,7 +121,7 @@ def test_mixed_parameter_parity_against_oracle(torch_cuda):
     orc, spread = PY.oracle_with_spread(descs, y0, phi0, sid)
     with Bd.System(descs) as S:
         g = Bd.to_numpy(S.run(y0, phi0, sid, kernel=Bd.IA_KERNEL_PERSISTENT))
-    rep = PY.compare(g, orc, spread, max_flip=0.05)
+    rep = PY.compare(g, orc, spread)
     print("C4 parity", rep)
     rep2 = PY.statistics_agree(g, orc)
     print("C4 statistics", rep2)
