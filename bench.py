@@ -56,6 +56,8 @@ def parse(argv=None):
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--stride", type=int, default=1, help="grid stride of the batch (1: the whole sweep)")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--last-part", type=float, default=0.0,
+                   help="fraction of the queue in the last part (0: equal parts)")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -67,6 +69,7 @@ def parse(argv=None):
     p.add_argument("--tail-group", type=int, default=0)
     p.add_argument("--tail-blocks-per-sm", type=int, default=0)
     p.add_argument("--tail-sms", type=int, default=0)
+    p.add_argument("--tail-warps", type=int, default=0)
     p.add_argument("--diff-sample", type=int, default=16384,
                    help="trajectories of the differentiation workload timed through the tangent and adjoint "
                         "kernels (0: skip)")
@@ -389,7 +392,14 @@ def energy_scan(args):
         stats = Bd.stats_to_numpy(st)
         att = int((out["n_steps"].to(torch.int64) + out["n_rej"].to(torch.int64)).sum().item())
         mx = int((out["n_steps"] + out["n_rej"]).max().item())
+        # complexes that outlive one secular period of the ion (2 pi / omega, omega = q_x Omega / 2^(3/2)):
+        # a second pericentre within it is the trap swinging the ion back onto the receding atom
+        tau = (out["t_last_bounce"] - out["t_first_bounce"]).cpu().numpy()
+        nbh = out["n_bounce"].cpu().numpy()
+    t_sec = 2.0 * math.pi / (abs(systems[0].q[0]) * systems[0].Omega / (2.0 * math.sqrt(2.0)))
+    long_lived = ((nbh >= 2) & (tau >= t_sec)).reshape(n_cells, n_per).sum(axis=1)
     per_species = {}
+    uK = 1e6 / I.K_TO_HARTREE
     for sp in dict.fromkeys(names):
         cells = [c for c in range(n_cells) if names[c] == sp]
         E = energies[cells]
@@ -398,18 +408,25 @@ def energy_scan(args):
         fit = St.fit_threshold(E, k, m)
         d0 = systems[cells[0]]
         w0 = St.w0_3d(d0.m_atom, d0.m_ion, d0.Omega, d0.a[0], d0.q[0], 0.5 * d0.alpha)
-        uK = 1e6 / I.K_TO_HARTREE
+        kl = long_lived[cells]
+        fit_l = St.fit_threshold(E, kl, m)
         per_species[sp] = {"E_threshold_uK": fit["E_th"] * uK, "E_end_uK": fit["E_end"] * uK, "W0_3D_uK": w0 * uK,
                            "threshold_over_W0": fit["E_th"] / w0, "end_over_W0": fit["E_end"] / w0,
                            "P0": fit["P0"], "P_inf": fit["P_inf"], "width_ln_E": fit["width_ln"],
                            "chi2_per_dof": fit["chi2"] / max(fit["dof"], 1),
-                           "P_complex_lowest_E": float(k[0] / m[0]), "P_complex_highest_E": float(k[-1] / m[-1])}
+                           "P_complex_lowest_E": float(k[0] / m[0]), "P_complex_highest_E": float(k[-1] / m[-1]),
+                           "beyond_one_secular_period": {
+                               "E_threshold_uK": fit_l["E_th"] * uK, "E_end_uK": fit_l["E_end"] * uK,
+                               "end_over_W0": fit_l["E_end"] / w0, "P0": fit_l["P0"], "P_inf": fit_l["P_inf"],
+                               "chi2_per_dof": fit_l["chi2"] / max(fit_l["dof"], 1),
+                               "P_lowest_E": float(kl[0] / m[0]), "P_highest_E": float(kl[-1] / m[-1])}}
     desc = (f"collision-energy scan: Yb+ head-on with {', '.join(dict.fromkeys(names))}, "
             f"{n_cells // len(per_species)} energies 30 nK..1 mK, {n_per} trajectories per energy, r0 = 20,000 a0, "
             f"D_e = 1 K, q = 0.1, t_max = 3 ms, random rf phase; initial conditions drawn on the device")
     print(json.dumps({"metric": METRIC, "workload": "energy-scan", "value": n / (ms / 1e3), "unit": UNIT, "ms": ms,
                       "trajectories": n, "attempted_steps_per_trajectory": att / n, "max_attempted_steps": mx,
                       "wait_errors": waits, "gpu_launches": n_cells + 4, "dtype": "f64", "data": "synthetic",
+                      "secular_period_us": t_sec * I.AU_TIME_S * 1e6,
                       "config": {"workload": desc, "rtol": 1e-10}, "per_species": per_species}), flush=True)
 
 
@@ -763,9 +780,15 @@ def sweep_in_queue_order(stride: int, offset: int):
     return systems, hy, hp, hs, order
 
 
-def part_bounds(n: int, parts: int) -> np.ndarray:
-    """Queue positions where each of `parts` equal parts of an n-trajectory batch starts (and n)."""
-    return np.linspace(0, n, parts + 1).round().astype(np.int64)
+def part_bounds(n: int, parts: int, last_frac: float = 0.0) -> np.ndarray:
+    """Queue positions where each of `parts` parts of an n-trajectory batch starts (and n): equal parts,
+    or, with last_frac > 0, the last part holding that fraction of the queue (its cheapest trajectories:
+    bulk work that overlaps the tail's last complexes instead of leaving the GPU waiting for them) and
+    the others equal."""
+    if parts < 2 or last_frac <= 0.0:
+        return np.linspace(0, n, parts + 1).round().astype(np.int64)
+    head = int(round(n * (1.0 - last_frac)))
+    return np.concatenate([np.linspace(0, head, parts).round(), [n]]).astype(np.int64)
 
 
 def lane_options(args, handle, y, p, d, n_sample: int, attempt_cap: int):
@@ -777,7 +800,7 @@ def lane_options(args, handle, y, p, d, n_sample: int, attempt_cap: int):
     from paper_2509_15117_gb300 import binding as Bd
     kw = {"block": args.block, "refill": args.refill, "blocks_per_sm": args.blocks_per_sm,
           "regs_variant": args.regs_variant, "slice_budget": args.slice_budget, "tail_group": args.tail_group,
-          "tail_blocks_per_sm": args.tail_blocks_per_sm, "tail_sms": args.tail_sms}
+          "tail_blocks_per_sm": args.tail_blocks_per_sm, "tail_sms": args.tail_sms, "tail_warps": args.tail_warps}
     tune = None
     if not args.no_autotune and args.block == 0:
         n = int(p.shape[0])
@@ -788,11 +811,11 @@ def lane_options(args, handle, y, p, d, n_sample: int, attempt_cap: int):
         tune = {"pick": pick, "best_ms": ms, "seconds": time.perf_counter() - t0,
                 "sample": f"{int(idx.numel())} trajectories drawn at random (seed 99) from the batch, every "
                           f"one stopped after {attempt_cap} attempted steps (lane phase only); 9 candidates "
-                          f"(block 64/128/256, register cap 1 or 3 blocks/SM, refill 1/4/16)"}
+                          f"(block 64/128/256, register cap 1 or 3 blocks/SM, refill 1/4/16), each timed twice"}
         kw.update(pick)
     block = kw["block"] or 128
     if args.tail_sms == 0:
-        kw["tail_sms"] = 128 // min(4, block // 32)
+        kw["tail_sms"] = 128 // min(kw["tail_warps"] or 4, block // 32)
     return kw, tune
 
 
@@ -843,7 +866,7 @@ def main():
     dy.copy_(hy)
     dp_.copy_(hp)
     ds.copy_(hs)
-    kw, tune = lane_options(args, sysh.handle, dy, dp_, ds, 131072, 1024)
+    kw, tune = lane_options(args, sysh.handle, dy, dp_, ds, 65536, 8192)
 
     # warm-up: W parts of a queue over the short trajectories of the workload (the 1 mK systems of
     # every 4th grid point), the same kernel and part logic as the timed steps
@@ -863,7 +886,7 @@ def main():
     peak_flops = Bd.ia_fp64_peak(4, 20000)
 
     Q = Bd.Queue(sysh.handle, n, **kw)
-    bounds = part_bounds(n, K)
+    bounds = part_bounds(n, K, args.last_part)
     fields = list(out.keys())
     # timed steps: host -> device copy of the part's inputs, L2 flush, the part's launch (device-timed
     # for `value`), device -> host copy of the part's observables (the last step copies every
@@ -986,6 +1009,8 @@ def main():
                             + f" ({int(n_all / world)} trajectories), integrated once over the {K} steps: step k is "
                               f"part k of one work queue over the batch in queue order",
                 "trajectories_per_step": int(n_all / K), "rtol": 1e-10, "kernel": "persistent (ia_queue)",
+                "parts": ("equal" if args.last_part <= 0 else
+                          f"the last holds {args.last_part:g} of the queue (its cheapest), the others equal"),
                 "queue_order": "systems by sqrt(m_atom)/speed, descending",
                 "l2": "256 MiB buffer written before each step (each part's inputs also exceed L2)",
                 "launch_options": {k_: v for k_, v in kw.items() if v},

@@ -342,9 +342,10 @@ int ia_graph_destroy(ia_graph* graph);
  * Autotuner of the persistent kernel's lane phase (block size, register cap, refill grain). Each
  * candidate integrates the n trajectories of `ic` (a sample of the batch to tune for) with every
  * trajectory stopped after `attempt_cap` attempted steps (no tail phase, outputs not written), timed
- * with CUDA events on `stream`; every candidate does the same arithmetic, so the fastest has the
- * highest lane-phase throughput. Writes the winner into *best (other fields copied from *base, which
- * may be NULL) and its time in *best_ms. Synchronous. attempt_cap: 64..1048576.
+ * with CUDA events on `stream`, twice (interleaved with the other candidates; the shorter time counts);
+ * every candidate does the same arithmetic, so the fastest has the highest lane-phase throughput.
+ * Writes the winner into *best (other fields copied from *base, which may be NULL) and its time in
+ * *best_ms. Synchronous. attempt_cap: 64..1048576.
  */
 int ia_autotune(ia_system* sys, const ia_ic_soa* ic, int64_t n, int32_t attempt_cap, const ia_launch_opts* base,
                 ia_launch_opts* best, double* best_ms, void* stream);

@@ -189,9 +189,7 @@ __device__ __forceinline__ int prim_attempt(const SysDev& P, const TLane& tl, in
     const bool prim = tl.dir == 0;
     const bool accept = (__ballot_sync(FULL, prim && !(okx && okv)) & 0x3fu) == 0;
     const bool finite = (__ballot_sync(FULL, prim && !(fx && fv)) & 0x3fu) == 0;
-    float errf;
-    double errd;
-    group_err(0, tl.comp, prim, rx, aex, scx, rv, aev, scv, errf, errd);
+    const ErrMeas em = group_err(0, tl.comp, prim, rx, aex, scx, rv, aev, scv);
     const int jj = tl.comp < 3 ? tl.comp : tl.comp - 3;
     const double wj = shfl(vn, 3 + jj) - shfl(vn, jj);
     const double w0 = shfl(wj, 0), w1 = shfl(wj, 1), w2 = shfl(wj, 2);
@@ -203,7 +201,7 @@ __device__ __forceinline__ int prim_attempt(const SysDev& P, const TLane& tl, in
         return PA_STOP;
     }
     if (!accept) {
-        st = on_reject(P, S, errd, errf);
+        st = on_reject(P, S, em);
         return st != 0xffffffffu ? PA_STOP : PA_REJ;
     }
     if (on_accept(P, S, rd, r2n0)) {
@@ -215,7 +213,7 @@ __device__ __forceinline__ int prim_attempt(const SysDev& P, const TLane& tl, in
     v = vn;
     a1 = a7;
     c1 = cs67;
-    on_commit(P, S, errd, errf);
+    on_commit(P, S, em);
     return PA_COMMIT;
 }
 

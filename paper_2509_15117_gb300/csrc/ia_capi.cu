@@ -456,9 +456,7 @@ __device__ __forceinline__ int tail_phase(const SysDev* __restrict__ tab, const 
         const unsigned gmask = ((1u << G) - 1u) << gl.base;
         const bool accept = (__ballot_sync(FULL, !ok) & gmask) == 0;
         const bool finite = (__ballot_sync(FULL, !fi) & gmask) == 0;
-        float errf;
-        double errd;
-        group_err(gl.base, gl.c, real, rx, aex, scx, rv, aev, scv, errf, errd);
+        const ErrMeas em = group_err(gl.base, gl.c, real, rx, aex, scx, rv, aev, scv);
         // radial velocity sign at the step end: d . (v_a - v_i)
         const int j = gl.comp < 3 ? gl.comp : gl.comp - 3;
         const double wj = shfl(vn, gl.base + 3 + j) - shfl(vn, gl.base + j);
@@ -473,7 +471,7 @@ __device__ __forceinline__ int tail_phase(const SysDev* __restrict__ tab, const 
                 res = 1;
                 st = ST_NONFINITE;
             } else if (!accept) {
-                st = on_reject(P, S, errd, errf);
+                st = on_reject(P, S, em);
                 if (st != 0xffffffffu) res = 1;
             } else if (on_accept(P, S, rd, r2new)) {
                 res = 2;
@@ -481,7 +479,7 @@ __device__ __forceinline__ int tail_phase(const SysDev* __restrict__ tab, const 
                 x = xn;
                 v = vn;
                 a1 = a7;
-                on_commit(P, S, errd, errf);
+                on_commit(P, S, em);
             }
         }
         if (__any_sync(FULL, res != 0)) {
@@ -547,7 +545,8 @@ struct __align__(16) PairShared {
     double rd[32];      // helper -> chain: d . (v_a - v_i) at the step end
     long long ck[32];   // helper -> chain: claimed suspend record of the lane's group
     float errf[32];     // helper -> chain: FP32 error ratio of the lane's group
-    double errd[32];    // helper -> chain: its FP64 error measure
+    double err_ae[32];  // helper -> chain: |e| and sc of the component that sets it
+    double err_sc[32];
     int dec[32];        // helper -> chain: bit 0 accept, bit 1 finite
     int claim[32];      // helper -> chain: claim result of the lane's group (0..3, as in tail_phase)
     unsigned long long seq_h[32], seq_c[32];  // posts of the helper and of the chain warp, per lane
@@ -740,8 +739,7 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
         // values both warps hold at the end of the attempt
         double xn, vn, a7, r2new, rd;
         double a3 = 0.0, a4 = 0.0, a5 = 0.0, a6 = 0.0;  // helper: kept for the exit epilogue
-        float errf;
-        double errd;
+        ErrMeas em;
         bool accept, finite;
         if (helper) {
             // rf phases first: the chain warp needs the ion trap coefficient of stage 2 soonest.
@@ -829,12 +827,13 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
             const unsigned gmask = ((1u << G) - 1u) << gl.base;
             accept = (__ballot_sync(FULL, !okk) & gmask) == 0;
             finite = (__ballot_sync(FULL, !fi) & gmask) == 0;
-            group_err(gl.base, gl.c, real, rx, aex, scx, rv, aev, scv, errf, errd);
+            em = group_err(gl.base, gl.c, real, rx, aex, scx, rv, aev, scv);
             rd = fma(dn0, w0, fma(dn1, w1, dn2 * w2));
             sh->vn[lane] = vn;
             sh->rd[lane] = rd;
-            sh->errf[lane] = errf;
-            sh->errd[lane] = errd;
+            sh->errf[lane] = em.f;
+            sh->err_ae[lane] = em.ae;
+            sh->err_sc[lane] = em.sc;
             sh->dec[lane] = (accept ? 1 : 0) | (finite ? 2 : 0);
             pair_post(sh->seq_h, nh);                                     // H5: the decision
             if (!ok) broken = true;
@@ -892,8 +891,9 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
             ok = pair_wait(sh->seq_h, nh) && ok;                          // H5: the decision
             vn = sh->vn[lane];
             rd = sh->rd[lane];
-            errf = sh->errf[lane];
-            errd = sh->errd[lane];
+            em.f = sh->errf[lane];
+            em.ae = sh->err_ae[lane];
+            em.sc = sh->err_sc[lane];
             const int dec = sh->dec[lane];
             accept = (dec & 1) != 0;
             finite = (dec & 2) != 0;
@@ -909,7 +909,7 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
                 res = 1;
                 st = ST_NONFINITE;
             } else if (!accept) {
-                st = on_reject(P, S, errd, errf);
+                st = on_reject(P, S, em);
                 if (st != 0xffffffffu) res = 1;
             } else if (on_accept(P, S, rd, r2new)) {
                 res = 2;
@@ -917,7 +917,7 @@ __device__ __forceinline__ void tail_phase_pair(const SysDev* __restrict__ tab, 
                 x = xn;
                 v = vn;
                 a1 = a7;
-                on_commit(P, S, errd, errf);
+                on_commit(P, S, em);
             }
         }
         if (__any_sync(FULL, res != 0)) {
@@ -1193,9 +1193,7 @@ __global__ void __launch_bounds__(128) k_tangent(const SysDev* __restrict__ tab,
             const bool prim = tl.dir == 0;
             const bool accept = (__ballot_sync(FULL, prim && !(okx && okv)) & 0x3fu) == 0;
             const bool finite = (__ballot_sync(FULL, prim && !(fx && fv)) & 0x3fu) == 0;
-            float errf;
-            double errd;
-            group_err(0, lane, prim, rx, aex, scx, rv, aev, scv, errf, errd);
+            const ErrMeas em = group_err(0, lane, prim, rx, aex, scx, rv, aev, scv);
             const int jj = tl.comp < 3 ? tl.comp : tl.comp - 3;
             const double wj = shfl(vn, 3 + jj) - shfl(vn, jj);
             const double w0 = shfl(wj, 0), w1 = shfl(wj, 1), w2 = shfl(wj, 2);
@@ -1206,7 +1204,7 @@ __global__ void __launch_bounds__(128) k_tangent(const SysDev* __restrict__ tab,
                 break;
             }
             if (!accept) {
-                st = on_reject(P, S, errd, errf);
+                st = on_reject(P, S, em);
                 if (st != 0xffffffffu) {
                     res = 1;
                     break;
@@ -1220,7 +1218,7 @@ __global__ void __launch_bounds__(128) k_tangent(const SysDev* __restrict__ tab,
             x = xn;
             v = vn;
             a1 = a7;
-            on_commit(P, S, errd, errf);
+            on_commit(P, S, em);
             // exact power-of-two rescaling of a tangent direction that left [2^-256, 2^256]
             int me = max_exp3(x, v, a1);
 #pragma unroll
@@ -2160,10 +2158,13 @@ int ia_autotune(ia_system* sys, const ia_ic_soa* ic, int64_t n, int32_t attempt_
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int rc = IA_OK;
-    double best_t = 1e300;
-    Cand win = cands[0];
-    for (int c = -1; c < (int)(sizeof(cands) / sizeof(cands[0])) && rc == IA_OK; ++c) {
-        const Cand cd = cands[c < 0 ? 0 : c];  // c = -1: warm-up of the first candidate
+    constexpr int NC = (int)(sizeof(cands) / sizeof(cands[0]));
+    constexpr int PASSES = 2;  // every candidate timed twice, interleaved; its time is the shorter
+    double cand_t[NC];
+    for (int c = 0; c < NC; ++c) cand_t[c] = 1e300;
+    for (int it = -1; it < PASSES * NC && rc == IA_OK; ++it) {
+        const int c = it < 0 ? 0 : it % NC;  // it = -1: warm-up of the first candidate
+        const Cand cd = cands[c];
         const void* fn = sched_fn(cd.block, cd.minb, 6);
         int resident = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fn, cd.block, 0) != cudaSuccess || resident <= 0) {
@@ -2189,11 +2190,15 @@ int ia_autotune(ia_system* sys, const ia_ic_soa* ic, int64_t n, int32_t attempt_
         if (rc == IA_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = IA_ERR_CUDA;
         float ms = 0.0f;
         if (rc == IA_OK) cudaEventElapsedTime(&ms, e0, e1);
-        if (c >= 0 && rc == IA_OK && ms < best_t) {
-            best_t = ms;
-            win = cd;
-        }
+        if (it >= 0 && rc == IA_OK && ms < cand_t[c]) cand_t[c] = ms;
     }
+    double best_t = 1e300;
+    Cand win = cands[0];
+    for (int c = 0; c < NC; ++c)
+        if (cand_t[c] < best_t) {
+            best_t = cand_t[c];
+            win = cands[c];
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(obuf);

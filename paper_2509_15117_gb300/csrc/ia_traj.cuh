@@ -301,9 +301,10 @@ __device__ __forceinline__ void err_check(double rtol, double atol, double y_old
 }
 
 // ode45's error measure err = max_k |e_k| / sc_k over the twelve components. The components' ratios
-// are compared in FP32; the largest (ties to the lowest index k in the order x_ion0, v_ion0, x_ion1,
-// ..., x_atom2, v_atom2, the same in every layout) is then formed in FP64, so that the step-size rules
-// see the error measure the oracle sees, to a few ulps.
+// are compared in FP32; the step-size rules then use the winner's |e| and sc in FP64 (ties go to the
+// lowest index k in the order x_ion0, v_ion0, x_ion1, ..., x_atom2, v_atom2, the same in every layout),
+// so that the step sizes follow the oracle's rules to far below the ~1e-8 by which the two sides' error
+// estimates (differences of O(h) terms, summed in different orders) differ anyway.
 struct ErrMax {
     unsigned long long key;  // bits of the FP32 ratio << 32 | (15 - k): larger key = larger ratio, lower k
     double ae, sc;
@@ -321,37 +322,39 @@ __device__ __forceinline__ void err_take(ErrMax& m, float ratio, int k, double a
         m.sc = sc;
     }
 }
-// The measure itself: |e| / sc of the winning component in FP64 (sc > 0: atol > 0).
-__device__ __forceinline__ double err_measure(double ae, double sc) { return ae * rcp_nr(sc); }
 
-// err^(-1/5) for err in [0.16^5, 0.125^-5] (where the step-size factor is not clamped): the FP32 value
-// exp2(-0.2 log2 err) (relative error ~2^-21) refined by two Newton steps on err y^5 = 1, each of
-// which squares the relative error (y <- y (1 - (err y^5 - 1)/5) leaves 3 eps^2): ~2^-40, then below
-// the FP64 rounding of the arithmetic.
-__device__ __forceinline__ double err_pow_m02(double err, float errf)
+// The error measure as the step-size rules use it: its FP32 value errf and, in FP64, the winning
+// component's |e| and sc (err = ae / sc).
+struct ErrMeas {
+    float f;
+    double ae, sc;
+};
+
+// err^(-1/5) for err = ae/sc in [0.16^5, 0.125^-5] (where the factor is not clamped): the FP32 value
+// y = exp2(-0.2 log2 errf) (relative error ~2^-21) refined by one Newton step on err y^5 = 1,
+// y <- y (1 - r/5), r = (ae y^5 - sc)/sc, which leaves 3 eps^2 ~ 2^-40; r is small, so forming it with
+// the FP32 reciprocal of sc costs only ~2^-23 of it (~2^-46 in y).
+__device__ __forceinline__ double err_pow_m02(const ErrMeas& e)
 {
-    double y = pos_float_to_double(exp2f(-0.2f * __log2f(errf)));
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const double y2 = y * y;
-        const double y5 = (y2 * y2) * y;
-        const double r = fma(err, y5, -1.0);
-        y = fma(-0.2 * y, r, y);
-    }
-    return y;
+    const double y = pos_float_to_double(exp2f(-0.2f * __log2f(e.f)));
+    const double y2 = y * y;
+    const double y5 = (y2 * y2) * y;
+    const double inv_sc = pos_float_to_double(rcp_approx_f32(nn_to_float(e.sc)));
+    const double r = fma(e.ae, y5, -e.sc) * inv_sc;
+    return fma(-0.2 * y, r, y);
 }
 
-// Step-size factors of ode45 (Shampine & Reichelt 1997) from the error measure err (FP64) and its FP32
-// value errf. After an accepted step: h / (1.25 err^(1/5)) = h 0.8 err^(-1/5) when 1.25 err^(1/5) > 0.2,
-// i.e. err > 0.16^5, else 5 h.
-__device__ __forceinline__ double grow_factor(double err, float errf)
+// Step-size factors of ode45 (Shampine & Reichelt 1997). After an accepted step:
+// h / (1.25 err^(1/5)) = h 0.8 err^(-1/5) when 1.25 err^(1/5) > 0.2, i.e. err > 0.16^5, else 5 h (the
+// clamps decide on errf: the factor is continuous there).
+__device__ __forceinline__ double grow_factor(const ErrMeas& e)
 {
-    return nn_lt(1.048576e-4, err) ? 0.8 * err_pow_m02(err, errf) : 5.0;
+    return (e.f > 1.048576e-4f) ? 0.8 * err_pow_m02(e) : 5.0;
 }
 // After a first failure: max(0.1, 0.8 err^(-1/5)); the floor holds from err = 0.125^-5 = 32768 on.
-__device__ __forceinline__ double shrink_factor(double err, float errf)
+__device__ __forceinline__ double shrink_factor(const ErrMeas& e)
 {
-    return nn_lt(err, 32768.0) ? nn_max(0.1, 0.8 * err_pow_m02(err, errf)) : 0.1;
+    return (e.f < 32768.0f) ? nn_max(0.1, 0.8 * err_pow_m02(e)) : 0.1;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -474,7 +477,7 @@ __device__ __forceinline__ uint32_t attempt_begin(const SysDev& P, Scal& S)
 
 // After the error test of an attempt: bookkeeping of a rejection. Returns a stop status or
 // 0xffffffff to go on (the attempt is repeated with the smaller h).
-__device__ __forceinline__ uint32_t on_reject(const SysDev& P, Scal& S, double err, float errf)
+__device__ __forceinline__ uint32_t on_reject(const SysDev& P, Scal& S, const ErrMeas& em)
 {
     const double h = S.h;
     S.n_rej += 1;
@@ -482,7 +485,7 @@ __device__ __forceinline__ uint32_t on_reject(const SysDev& P, Scal& S, double e
     double fac;
     if (S.nofailed) {
         S.nofailed = false;
-        fac = shrink_factor(err, errf);  // max(0.1, 0.8 err^(-1/5))
+        fac = shrink_factor(em);  // max(0.1, 0.8 err^(-1/5))
     } else {
         fac = 0.5;
     }
@@ -508,11 +511,11 @@ __device__ __forceinline__ bool on_accept(const SysDev& P, Scal& S, double rd, d
     return nn_le(P.r0sq, r2new) && dbits(rd) > 0;  // rd > 0
 }
 
-__device__ __forceinline__ void on_commit(const SysDev& P, Scal& S, double err, float errf)
+__device__ __forceinline__ void on_commit(const SysDev& P, Scal& S, const ErrMeas& em)
 {
     const double t = S.t, h = S.h;
     S.t = nn_le(P.t_max, t + h) ? P.t_max : t + h;
-    if (S.nofailed) S.h = h * grow_factor(err, errf);
+    if (S.nofailed) S.h = h * grow_factor(em);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -726,10 +729,9 @@ __device__ __forceinline__ int lane_attempt(const SysDev& P, Lane& L, Final& fin
             fin.status = ST_NONFINITE;
             goto stop_here;
         }
-        const float errf = __uint_as_float((unsigned)(em.key >> 32));
-        const double errd = err_measure(em.ae, em.sc);
+        const ErrMeas emeas{__uint_as_float((unsigned)(em.key >> 32)), em.ae, em.sc};
         if (!accept) {
-            st = on_reject(P, L.s, errd, errf);
+            st = on_reject(P, L.s, emeas);
             if (st != 0xffffffffu) {
                 fin.status = st;
                 goto stop_here;
@@ -758,7 +760,7 @@ __device__ __forceinline__ int lane_attempt(const SysDev& P, Lane& L, Final& fin
             L.xi[j] = xni[j]; L.xa[j] = xna[j]; L.vi[j] = vni[j]; L.va[j] = vna[j];
             L.a1i[j] = a7i[j]; L.a1a[j] = a7a[j];
         }
-        on_commit(P, L.s, errd, errf);
+        on_commit(P, L.s, emeas);
         return RUNNING;
     }
 stop_here:
@@ -953,10 +955,10 @@ __device__ __forceinline__ double accel_group(const SysDev& P, const GroupLane<G
 
 // Error measure of a trajectory held by lanes base .. base + 5 (lane base + c holds component c of
 // [x_ion, x_atom], whose position and velocity are components k = 2c and 2c + 1 of the measure): the
-// largest FP32 ratio of the group, ties to the lowest k (as in lane mode), and that component's FP64
-// ratio, identical on every lane. real = false on lanes outside the six.
-__device__ __forceinline__ void group_err(int base, int c, bool real, float rx, double aex, double scx, float rv,
-                                          double aev, double scv, float& errf, double& errd)
+// largest FP32 ratio of the group, ties to the lowest k (as in lane mode), with that component's |e|
+// and sc, identical on every lane. real = false on lanes outside the six.
+__device__ __forceinline__ ErrMeas group_err(int base, int c, bool real, float rx, double aex, double scx, float rv,
+                                             double aev, double scv)
 {
     const unsigned long long kx = real ? err_key(rx, 2 * c) : 0ull;
     const unsigned long long kv = real ? err_key(rv, 2 * c + 1) : 0ull;
@@ -970,9 +972,11 @@ __device__ __forceinline__ void group_err(int base, int c, bool real, float rx, 
         best = o > best ? o : best;
     }
     const int src = base + ((15 - (int)(best & 15ull)) >> 1);
-    const double aw = shfl(ae, src), sw = shfl(sc, src);
-    errf = __uint_as_float((unsigned)(best >> 32));
-    errd = best == 0ull ? 0.0 : err_measure(aw, sw);
+    ErrMeas e;
+    e.f = __uint_as_float((unsigned)(best >> 32));
+    e.ae = shfl(ae, src);
+    e.sc = shfl(sc, src);
+    return e;
 }
 
 // Result of a trajectory whose sys_id is outside the table: its initial state, BAD_IC.

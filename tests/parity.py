@@ -15,11 +15,10 @@ Bars, on trajectories that end with one bounce on both sides (the regular, non-c
   - every trajectory: |gpu - oracle| <= max(1e-8 |oracle|, 16 spread);
   - all but a fraction 0.002 (the maximum of nine runs underestimates a heavy-tailed noise now and
     then): |gpu - oracle| <= max(1e-8 |oracle|, 4 spread);
-  - distribution: the GPU's differences are distributed like the oracle's own differences under the
-    noise model (median and 90th percentile of log10 |diff|/|oracle| within 0.5 of each other), so a
-    systematic error hiding under the per-trajectory bars shows as a shift (checked where the
-    differences are not all a hundred times below the plain bar: the bounce times differ by ~1e-12
-    because the GPU forms the step-size factor in FP32, which the noise model does not imitate);
+  - distribution: the GPU's differences are not larger than the oracle's own differences under the
+    noise model (median and 90th percentile of log10 |diff|/|oracle| at most 0.5 above the model's), so
+    a systematic error hiding under the per-trajectory bars shows as a shift (checked where the
+    differences are not all a hundred times below the plain bar);
   - n_bounce is 1 on the GPU wherever the oracle's is 1 and none of the nine runs changes it; the
     complex flag may flip only on trajectories where the oracle's own runs flip it (at most twice their
     count plus two).
@@ -116,7 +115,8 @@ def _check_field(name, g, o, s, o_noise, rep, rel=REL):
         dmed = float(np.median(lg) - np.median(ln))
         d90 = float(np.percentile(lg, 90) - np.percentile(ln, 90))
         rep[name + "_log10_shift_median_p90"] = (round(dmed, 3), round(d90, 3))
-        assert abs(dmed) <= 0.5 and abs(d90) <= 0.5, (name, "distribution shift", dmed, d90, rep)
+        # one-sided: differences larger than the oracle's own are what a kernel error would produce
+        assert dmed <= 0.5 and d90 <= 0.5, (name, "distribution shift", dmed, d90, rep)
 
 
 def compare(gpu: dict, orc: np.ndarray, spread: dict):

@@ -35,7 +35,7 @@ def test_whole_sweep_sampled_parity_and_invariants(torch_cuda):
     descs = [s.as_dict() for s in systems]
     with Bd.System(descs) as S:
         yd, pd, sd = hy.cuda(), hp.cuda(), hs.cuda()
-        kw, tune = bench.lane_options(args, S.handle, yd, pd, sd, 32768, 2048)
+        kw, tune = bench.lane_options(args, S.handle, yd, pd, sd, 65536, 8192)
         out = Bd.alloc_obs(n)
         bounds = bench.part_bounds(n, args.steps)
         with Bd.Queue(S.handle, n, **kw) as Q:
