@@ -44,8 +44,8 @@ GRID = 1024
 # executes more FP64 instructions in total, so this is the useful work per attempt.
 FLOPS_PER_ATTEMPT = 884.0
 # DRAM bytes per trajectory of the persistent kernel (read + write, ncu dram__bytes on the 512 x 512
-# bulk-only profile case: 38.8 MB for 262,144 trajectories): initial conditions in, observables out.
-DRAM_BYTES_PER_TRAJECTORY = 148.0
+# bulk-only profile case: 37.8 MB for 262,144 trajectories): initial conditions in, observables out.
+DRAM_BYTES_PER_TRAJECTORY = 144.0
 
 
 def parse(argv=None):
@@ -56,6 +56,12 @@ def parse(argv=None):
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--stride", type=int, default=1, help="grid stride of the batch (1: the whole sweep)")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--order", choices=("cost", "threshold"), default="cost",
+                   help="queue order of the sweep's systems: cost (sqrt(m_a)/v0 descending) or threshold "
+                        "(E / W0^3D ascending: the complex-forming systems first)")
+    p.add_argument("--dump-long", default="",
+                   help="write the queue position, system and attempted steps of every trajectory above "
+                        "2^17 attempts, with the part bounds and device times, to this .npz file")
     p.add_argument("--last-part", type=float, default=0.0,
                    help="fraction of the queue in the last part (0: equal parts)")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -759,7 +765,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def sweep_in_queue_order(stride: int, offset: int):
+def sweep_in_queue_order(stride: int, offset: int, rule: str = "cost"):
     """The species x energy sweep (every stride-th grid point from offset) laid out in queue order
     (systems by expected cost, costliest first; see schedule.py), so that each part of the queue is a
     contiguous range of the arrays. Returns the systems, the pinned host arrays (SoA state (12, n),
@@ -767,8 +773,15 @@ def sweep_in_queue_order(stride: int, offset: int):
     import torch
     from paper_2509_15117_gb300 import schedule as Sch
     systems, y0, phi0, sid = I.c2_workload(n_grid=GRID, stride=stride, offset=offset)
-    speeds = [I.speed_for_energy(I.kelvin(E), s.m_atom) for (sp, E, s) in I.c2_systems()]
-    order = Sch.order_by_cost(sid, Sch.system_cost(systems, speeds))
+    if rule == "threshold":
+        from paper_2509_15117_gb300 import statistics as St
+        w0 = [St.w0_3d(s.m_atom, s.m_ion, s.Omega, s.a[0], s.q[0], 0.5 * s.alpha) for s in systems]
+        energies = [I.kelvin(E) for (sp, E, s) in I.c2_systems()]
+        cost = Sch.system_cost_threshold(energies, w0)
+    else:
+        speeds = [I.speed_for_energy(I.kelvin(E), s.m_atom) for (sp, E, s) in I.c2_systems()]
+        cost = Sch.system_cost(systems, speeds)
+    order = Sch.order_by_cost(sid, cost)
     n = len(phi0)
     hy = torch.empty((12, n), dtype=torch.float64).pin_memory()
     hyn = hy.numpy()
@@ -851,7 +864,8 @@ def main():
     # The batch: the whole sweep (or with --stride S every S-th grid point, a different offset per rank)
     # in queue order, pinned on the host; the device holds the whole batch, and the K timed steps are
     # the K parts of one queue over it, so together they integrate every trajectory once.
-    systems, hy, hp, hs, order = sweep_in_queue_order(args.stride, step_offset(0, args.stride, rank, world))
+    systems, hy, hp, hs, order = sweep_in_queue_order(args.stride, step_offset(0, args.stride, rank, world),
+                                                      args.order)
     n = int(hp.shape[0])
     descs = [s.as_dict() for s in systems]
     sysh = Bd.System(descs)
@@ -941,6 +955,12 @@ def main():
     long_counts["attempts_beyond"] = {str(b): int(np.maximum(per - b, 0).sum())
                                       for b in (1 << 16, 1 << 17, 1 << 18, 1 << 19, 1 << 20)}
     long_counts["longest_queue_position"] = int(np.argmax(per)) / n
+    if args.dump_long and rank == 0:
+        q = np.nonzero(per > (1 << 17))[0]
+        sys_attempts = np.bincount(hs.numpy(), weights=per.astype(np.float64), minlength=len(systems))
+        np.savez(args.dump_long, position=q, sys_id=hs.numpy()[q], attempts=per[q], bounds=bounds,
+                 kernel_ms=np.asarray(kern_ms), n=n, sys_attempts=sys_attempts,
+                 sys_count=np.bincount(hs.numpy(), minlength=len(systems)), lane_ms=lane_ms)
     rhs = 6 * attempts + n
     tmax_ms, emax_ms = total_ms, float(sum(step_ms))
     if dist is not None:

@@ -344,6 +344,9 @@ int ia_graph_destroy(ia_graph* graph);
  * trajectory stopped after `attempt_cap` attempted steps (no tail phase, outputs not written), timed
  * with CUDA events on `stream`, twice (interleaved with the other candidates; the shorter time counts);
  * every candidate does the same arithmetic, so the fastest has the highest lane-phase throughput.
+ * Candidates within 1 % of the fastest count as equal, and among them the smallest refill grain wins
+ * (then the fastest): in the sample every trajectory stops at the same cap, which hides what a lazier
+ * refill costs in a batch of spread lengths.
  * Writes the winner into *best (other fields copied from *base, which may be NULL) and its time in
  * *best_ms. Synchronous. attempt_cap: 64..1048576.
  */

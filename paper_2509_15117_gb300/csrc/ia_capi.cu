@@ -2192,13 +2192,22 @@ int ia_autotune(ia_system* sys, const ia_ic_soa* ic, int64_t n, int32_t attempt_
         if (rc == IA_OK) cudaEventElapsedTime(&ms, e0, e1);
         if (it >= 0 && rc == IA_OK && ms < cand_t[c]) cand_t[c] = ms;
     }
+    // Candidates within 1 % of the fastest are treated as equal, and the smallest refill among them
+    // wins (then the fastest). The sample's trajectories all stop at the same cap, so lanes fall idle
+    // together and a lazier refill costs nothing there; in a whole batch lengths spread, and refilling
+    // each lane at once keeps warps fuller.
     double best_t = 1e300;
+    for (int c = 0; c < NC; ++c) best_t = cand_t[c] < best_t ? cand_t[c] : best_t;
     Cand win = cands[0];
-    for (int c = 0; c < NC; ++c)
-        if (cand_t[c] < best_t) {
-            best_t = cand_t[c];
+    double win_t = 1e300;
+    for (int c = 0; c < NC; ++c) {
+        if (cand_t[c] > best_t * 1.01) continue;
+        if (win_t == 1e300 || cands[c].refill < win.refill || (cands[c].refill == win.refill && cand_t[c] < win_t)) {
             win = cands[c];
+            win_t = cand_t[c];
         }
+    }
+    best_t = win_t;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(obuf);

@@ -20,6 +20,13 @@ def system_cost(systems, speeds) -> np.ndarray:
     return np.sqrt(m) / v
 
 
+def system_cost_threshold(energies, w0) -> np.ndarray:
+    """Relative cost per system from the complex-formation threshold: W0^3D / E, so that the systems
+    whose collision energy lies furthest below the heating energy scale W0^3D (where the complex
+    probability is highest, Fig. 4) come first. Energies and W0 in the same units."""
+    return np.asarray(w0, dtype=np.float64) / np.asarray(energies, dtype=np.float64)
+
+
 def order_by_cost(sys_id, cost) -> np.ndarray:
     """Permutation of 0..n-1 that visits trajectories of costlier systems first (stable within a system)."""
     sys_id = np.asarray(sys_id)
