@@ -44,8 +44,8 @@ GRID = 1024
 # executes more FP64 instructions in total, so this is the useful work per attempt.
 FLOPS_PER_ATTEMPT = 884.0
 # DRAM bytes per trajectory of the persistent kernel (read + write, ncu dram__bytes on the 512 x 512
-# bulk-only profile case: 37.8 MB for 262,144 trajectories): initial conditions in, observables out.
-DRAM_BYTES_PER_TRAJECTORY = 144.0
+# bulk-only profile case: 39.0 MB for 262,144 trajectories): initial conditions in, observables out.
+DRAM_BYTES_PER_TRAJECTORY = 148.8
 
 
 def parse(argv=None):
@@ -81,6 +81,8 @@ def parse(argv=None):
                         "kernels (0: skip)")
     p.add_argument("--diff-cap", type=int, default=1 << 16,
                    help="attempted steps after which each trajectory of that side measurement stops (0: none)")
+    p.add_argument("--workload-cap", type=int, default=0,
+                   help="with --workload diff: attempted steps after which each trajectory stops (0: none)")
     p.add_argument("--workload", default="sweep",
                    choices=["sweep", "thermal", "mixed-graph", "ftle", "diff", "sampler", "energy-scan",
                             "thermal-sweep", "lifetimes"],
@@ -203,7 +205,7 @@ def secondary(args):
     if args.workload == "diff":
         n = int(args.scale) if args.scale > 0 else 1 << 20
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-        tan, adj = diff_bench(n, flush, 0)
+        tan, adj = diff_bench(n, flush, args.workload_cap)
         print(json.dumps({"metric": METRIC, "workload": "diff", "tangent": tan, "adjoint": adj,
                           "gpu_launches": 6, "dtype": "f64", "data": "synthetic"}), flush=True)
         return
