@@ -63,6 +63,35 @@ def test_queue_order_puts_costly_systems_first_and_keeps_the_rest_stable():
     assert list(order) == [1, 3, 6, 2, 5, 0, 4]
 
 
+def test_threshold_order_puts_the_systems_furthest_below_w0_first():
+    from paper_2509_15117_gb300 import statistics as St
+    c2 = I.c2_systems()
+    systems = [s for (_, _, s) in c2]
+    energies = [I.kelvin(E) for (_, E, _) in c2]
+    w0 = [St.w0_3d(s.m_atom, s.m_ion, s.Omega, s.a[0], s.q[0], 0.5 * s.alpha) for s in systems]
+    cost = Sch.system_cost_threshold(energies, w0)
+    assert np.allclose(cost, np.asarray(w0) / np.asarray(energies), rtol=0, atol=0)
+    names = [(sp, E) for (sp, E, _) in c2]
+    ranked = [names[i] for i in np.argsort(-cost, kind="stable")]
+    assert ranked[0] == ("Cs", 1e-6) and ranked[-1] == ("Li", 1e-3)
+    # at one energy the heavier atom (larger W0^3D) comes first
+    at_1uK = [sp for (sp, E) in ranked if E == 1e-6]
+    assert at_1uK == ["Cs", "Rb", "K", "Na", "Li"]
+
+
+def test_part_bounds_cover_the_queue_once():
+    import bench
+    for n, parts in ((41943040, 20), (1000, 7), (5, 20), (1, 1)):
+        b = bench.part_bounds(n, parts)
+        assert b[0] == 0 and b[-1] == n and len(b) == parts + 1
+        assert np.all(np.diff(b) >= 0)
+        assert np.diff(b).max() - np.diff(b).min() <= 1
+    b = bench.part_bounds(1000, 5, 0.25)
+    assert b[0] == 0 and b[-1] == 1000 and len(b) == 6
+    head = np.diff(b)[:-1]
+    assert b[-1] - b[-2] == 250 and head.sum() == 750 and head.max() - head.min() <= 1
+
+
 stats = pytest.importorskip("scipy.stats")
 
 
