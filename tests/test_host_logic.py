@@ -141,3 +141,25 @@ def test_host_micromotion_covariance():
         cov = np.mean(y[:, j] * y[:, 3 + j])
         sd = math.sqrt(sv ** 2 + (k * sx) ** 2)
         assert abs(cov - (-k * sx * sx)) < 5 * sx * sd / math.sqrt(n), j
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference (the oracle on the host cores, bounded samples of the sweep) prints one
+    JSON line with the fields of the bench contract and the reference arm's own."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1",
+                        "--cpu-seconds", "2"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["unit"] == "trajectories/s" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["dtype"] == "f64" and d["data"] == "synthetic"
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
