@@ -230,16 +230,18 @@ int ia_static_phases(ia_system* sys, double* lane_ms, double* total_ms, int64_t*
  *   - trajectories past opts->slice_budget attempted steps go to suspend records and run in group mode
  *     on the reserved SMs, across parts, exactly as in ia_launch;
  *   - a part that does not take the last queue positions ends as soon as its queue is exhausted: every
- *     running trajectory is saved (lane mode: a carry record; group mode: a suspend record) and the
- *     next part continues it where it stopped;
+ *     running trajectory is saved (lane mode: a lane-mode carry record; group mode: a group-mode carry
+ *     record, or a suspend record when those are full) and the next part continues it where it
+ *     stopped, its group-mode carry records before any suspend record;
  *   - the part that takes the last positions finishes every trajectory before it returns.
  * Results are bit-identical to ia_launch (the plain kernel) whatever the split. A trajectory's
  * observables are written by the part in which it ends; after the last part all n are written.
  *
  * ia_queue_create: fixes the launch options (kernel persistent; opts->scratch must be NULL and
  *   opts->tail_pair not 1: the paired tail is not available here) and allocates the queue's device
- *   scratch (cudaMalloc, synchronous): counters, suspend records as in ia_scratch_bytes(n, opts), and
- *   two carry buffers of one 256-byte record per lane of the grid. Every block of the grid must be
+ *   scratch (cudaMalloc, synchronous): counters, suspend records as in ia_scratch_bytes(n, opts), two
+ *   lane-mode carry buffers of one 256-byte record per lane of the grid, and two group-mode carry
+ *   buffers of 5 records per tail warp. Every block of the grid must be
  *   resident (cooperative launch); otherwise IA_ERR_INVALID_ARG (a grid too large) or IA_ERR_NO_DEVICE.
  *   n >= 1.
  * ia_queue_launch: launches the next part on `stream` (asynchronous). ic and out describe the whole
